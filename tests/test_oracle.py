@@ -1,0 +1,380 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each check uses an independent
+route (a closed form, brute-force support enumeration, Lawson-Hanson from
+SciPy, numpy's matmul, a finite-difference gradient, or an invariant stated in
+§4.1) so that a dropped term, wrong sign or swapped index in ``oracle.c``
+fails at least one of them.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as WL
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+CONVERGE = dict(max_inner=20000, eps=0.0, abs_tol=1e-26, cd_steps=-1)
+
+
+def brute_force_nqp(Q, q):
+    """Support enumeration: the minimiser of 1/2 x'Qx + q'x, x >= 0, for Q > 0
+    is the unique x with x_S = -Q_SS^{-1} q_S >= 0 and (Qx + q)_{S^c} >= 0."""
+    r = len(q)
+    best = None
+    for k in range(r + 1):
+        for S in itertools.combinations(range(r), k):
+            x = np.zeros(r)
+            if S:
+                S = list(S)
+                x[S] = np.linalg.solve(Q[np.ix_(S, S)], -q[S])
+                if np.any(x[S] < -1e-12):
+                    continue
+            gr = Q @ x + q
+            comp = [i for i in range(r) if i not in (S or [])]
+            if comp and np.any(gr[comp] < -1e-9):
+                continue
+            f = 0.5 * x @ Q @ x + q @ x
+            if best is None or f < best[1]:
+                best = (np.maximum(x, 0), f)
+    return best[0]
+
+
+# ----------------------------------------------------------------- worked example
+def test_worked_example_closed_form_and_59_steps():
+    g = json.load(open(os.path.join(GOLD, "worked_example.json")))
+    H, h, x0 = (np.array(g[k]) for k in ("H", "h", "x0"))
+    xs = np.array(g["x_star_closed_form"])
+    # converged Alg. 3 hits the closed-form interior optimum
+    x, k, s = O.nqp(H, h, x0, O.nqp_opts(**CONVERGE))
+    np.testing.assert_allclose(x, xs, rtol=1e-12)
+    # plain exact-line-search gradient (no rescale, no coordinate part): 59 steps
+    tol = g["plain_line_search_stop_abs_sq_grad"]
+    x, k, s = O.nqp(H, h, x0, O.nqp_opts(max_inner=1000, eps=0.0, abs_tol=tol, cd_steps=0,
+                                         rescale=0))
+    assert k == g["plain_line_search_steps"]
+    # the same method on the rescaled problem (Eq. 5) needs far fewer steps
+    x, k2, s = O.nqp(H, h, x0, O.nqp_opts(max_inner=1000, eps=0.0, abs_tol=tol, cd_steps=0,
+                                          rescale=1))
+    assert k2 <= 4
+    Qt, d, dead = O.rescale(H)
+    assert abs(Qt[0, 1] - g["rescaled_Q_offdiag"]) < 1e-15
+    np.testing.assert_allclose(d, [1.0, np.sqrt(10.0)], rtol=1e-15)
+
+
+# ----------------------------------------------------------------- exact optima
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("beta,alpha", [(0.0, 0.0), (0.3, 0.0), (0.0, 0.7), (0.1, 0.05)])
+def test_nqp_matches_brute_force(r, beta, alpha):
+    for seed in range(6):
+        A, B = WL.random_nqp(1000 * r + seed, r, rows=1)
+        b = B[0] - 0.5          # mixed-sign targets give mixed active sets
+        Q = A.T @ A + beta * np.eye(r)
+        q = -(A.T @ b) + alpha
+        xb = brute_force_nqp(Q, q)
+        x0 = WL.rng(seed).random(r)
+        x, k, s = O.nqp(Q, q, x0, O.nqp_opts(**CONVERGE))
+        np.testing.assert_allclose(x, xb, rtol=1e-9, atol=1e-10)
+
+
+def test_nqp_matches_lawson_hanson():
+    so = pytest.importorskip("scipy.optimize")
+    for r in (8, 10, 20, 50):
+        for seed in range(3):
+            A, B = WL.random_nqp(77 + seed, r, k=2 * r + 5, rows=1)
+            b = B[0] * 2 - 0.6
+            xl, _ = so.nnls(A, b)
+            x, k, s = O.nqp(O.gram(A), -(A.T @ b), np.ones(r), O.nqp_opts(**CONVERGE))
+            np.testing.assert_allclose(x, xl, rtol=1e-7, atol=1e-9)
+
+
+def test_nqp_kkt_at_convergence():
+    for r in (7, 16, 33):
+        A, B = WL.random_nqp(5 + r, r, rows=20)
+        Q = O.gram(A, 0.0)
+        Cm = O.cross_dense(B - 0.4, A)
+        X, it, tot, _ = O.nnls_update(Q, Cm, 0.01, np.ones((20, r)), O.nqp_opts(**CONVERGE))
+        res = O.kkt(Q, Cm, 0.01, X)
+        assert np.all(X >= 0)
+        assert res[0] < 1e-9 and res[1] < 1e-9
+        # independent KKT check in numpy
+        G = X @ Q.T - Cm + 0.01
+        assert G.min() > -1e-9
+        assert np.abs(X * G).max() < 1e-9
+
+
+def test_r1_closed_form():
+    for c, q11, alpha, beta in [(3.0, 2.0, 0.0, 0.0), (-1.0, 2.0, 0.0, 0.5), (2.0, 0.5, 0.4, 0.1),
+                                (0.3, 1.0, 0.5, 0.0)]:
+        x, k, s = O.nqp(np.array([[q11 + beta]]), np.array([-c + alpha]), np.array([1.7]),
+                        O.nqp_opts(**CONVERGE))
+        assert abs(x[0] - max(0.0, (c - alpha) / (q11 + beta))) < 1e-14
+
+
+def test_diagonal_q_one_iteration_exact():
+    g = WL.rng(3)
+    for r in (3, 9, 40):
+        Q = np.diag(g.random(r) + 0.1)
+        q = g.normal(size=r)
+        for pg in (0, 1):
+            x, k, s = O.nqp(Q, q, g.random(r) * 3, O.nqp_opts(max_inner=1, eps=0.0, pg=pg))
+            np.testing.assert_allclose(x, np.maximum(0, -q / np.diag(Q)), rtol=1e-13, atol=1e-15)
+
+
+def test_dead_component_held_at_zero():
+    # an all-zero factor column and beta = 0 give H_ii = 0
+    g = WL.rng(11)
+    A = g.random((12, 4))
+    A[:, 2] = 0.0
+    b = g.random(12)
+    x, k, s = O.nqp(O.gram(A), -(A.T @ b), np.ones(4), O.nqp_opts(**CONVERGE))
+    assert x[2] == 0.0
+    keep = [0, 1, 3]
+    xb = brute_force_nqp(O.gram(A[:, keep]), -(A[:, keep].T @ b))
+    np.testing.assert_allclose(x[keep], xb, rtol=1e-9, atol=1e-12)
+
+
+# ----------------------------------------------------------------- rescale
+def test_rescale_invariants():
+    g = WL.rng(5)
+    for r in (1, 4, 10, 50, 128):
+        X = g.random((300, r))
+        H = O.gram(X, 0.0)
+        Qt, d, dead = O.rescale(H)
+        assert not dead.any()
+        np.testing.assert_array_equal(np.diag(Qt), np.ones(r))
+        # Qt_ij = cos(X_i, X_j) in [0, 1] for nonnegative columns (§4.1)
+        cos = (X.T @ X) / np.outer(np.linalg.norm(X, axis=0), np.linalg.norm(X, axis=0))
+        off = ~np.eye(r, dtype=bool)
+        np.testing.assert_allclose(Qt[off], cos[off], rtol=1e-12)
+        assert Qt.min() >= 0 and Qt.max() <= 1 + 1e-15
+        fro = np.linalg.norm(Qt)
+        assert np.sqrt(r) - 1e-12 <= fro <= r + 1e-12
+        np.testing.assert_allclose(d, np.linalg.norm(X, axis=0), rtol=1e-13)
+        # f(x) = ft(x .* d) (Eq. 3)
+        h = g.normal(size=r)
+        x = g.random(r)
+        f = 0.5 * x @ H @ x + h @ x
+        y = x * d
+        ft = 0.5 * y @ Qt @ y + (h / d) @ y
+        assert abs(f - ft) <= 1e-12 * max(1.0, abs(f))
+
+
+# ----------------------------------------------------------------- plain definitions
+def test_gram_and_cross_match_numpy():
+    g = WL.rng(9)
+    X = g.random((123, 17))
+    np.testing.assert_allclose(O.gram(X, 0.25), X.T @ X + 0.25 * np.eye(17), rtol=1e-13)
+    A = g.random((37, 91))
+    B = g.random((91, 13))
+    np.testing.assert_allclose(O.cross_dense(A, B), A @ B, rtol=1e-13)
+    rp, ci, va = WL.random_csr(4, 50, 91, 0.1, empty_rows=5, long_rows=2)
+    D = np.zeros((50, 91))
+    for i in range(50):
+        D[i, ci[rp[i]:rp[i + 1]]] = va[rp[i]:rp[i + 1]]
+    np.testing.assert_allclose(O.cross_csr(rp, ci, va, B), D @ B, rtol=1e-13)
+    trp, tci, tva = WL.csr_transpose(rp, ci, va, 50, 91)
+    Dt = np.zeros((91, 50))
+    for i in range(91):
+        Dt[i, tci[trp[i]:trp[i + 1]]] = tva[trp[i]:trp[i + 1]]
+    np.testing.assert_array_equal(Dt, D.T)
+
+
+def test_objectives_agree_and_match_numpy():
+    inst = WL.tiny(seed=2, r=6, m=40, n=30)
+    W, Ht = inst.W0, inst.Ht0
+    aw, ah, bw, bh = 0.1, 0.2, 0.3, 0.4
+    ref = (0.5 * np.sum((inst.V - W @ Ht.T) ** 2) + aw * W.sum() + ah * Ht.sum()
+           + 0.5 * bw * np.sum(W * W) + 0.5 * bh * np.sum(Ht * Ht))
+    J = O.objective_dense(inst.V, W, Ht, aw, ah, bw, bh)
+    assert abs(J - ref) <= 1e-12 * ref
+    # the CSR form uses the trace identity: an independent formula
+    rp = np.arange(0, 40 * 30 + 1, 30, dtype=np.int64)
+    ci = np.tile(np.arange(30, dtype=np.int32), 40)
+    J2 = O.objective_csr(rp, ci, inst.V.ravel(), 40, 30, W, Ht, aw, ah, bw, bh)
+    assert abs(J2 - ref) <= 1e-10 * ref
+
+
+# ----------------------------------------------------------------- penalties (§3.5)
+def test_penalties_enter_q_and_linear_term():
+    """Q = X'X + beta I and q = -c + alpha: the gradient of the per-row
+    penalised objective equals Qx + q (finite differences), and the NQP
+    solution minimises it (compared with a bound-constrained L-BFGS-B)."""
+    so = pytest.importorskip("scipy.optimize")
+    g = WL.rng(21)
+    Ht = g.random((25, 5))
+    v = g.random(25)
+    alpha, beta = 0.3, 0.7
+
+    def phi(x):
+        return 0.5 * np.sum((v - Ht @ x) ** 2) + alpha * x.sum() + 0.5 * beta * x @ x
+
+    Q = O.gram(Ht, beta)
+    c = O.cross_dense(v[None, :], Ht)[0]
+    x = g.random(5)
+    fd = np.array([(phi(x + 1e-6 * e) - phi(x - 1e-6 * e)) / 2e-6 for e in np.eye(5)])
+    np.testing.assert_allclose(Q @ x - c + alpha, fd, rtol=1e-6)
+    xs, k, s = O.nqp(Q, -c + alpha, np.ones(5), O.nqp_opts(**CONVERGE))
+    res = so.minimize(phi, np.ones(5), method="L-BFGS-B", bounds=[(0, None)] * 5,
+                      options=dict(ftol=1e-15, gtol=1e-12, maxiter=10000))
+    assert phi(xs) <= res.fun + 1e-9
+    np.testing.assert_allclose(xs, res.x, atol=1e-5)
+    # alpha shifts only the linear term, beta only the diagonal
+    np.testing.assert_allclose(O.gram(Ht, beta) - O.gram(Ht, 0.0), beta * np.eye(5), atol=1e-14)
+    X1, *_ = O.nnls_update(Q, c[None, :], 0.0, np.ones((1, 5)), O.nqp_opts(**CONVERGE))
+    X2, *_ = O.nnls_update(Q, c[None, :] - alpha, 0.0, np.ones((1, 5)), O.nqp_opts(**CONVERGE))
+    np.testing.assert_allclose(X2[0], xs, rtol=1e-10, atol=1e-14)
+    X3, *_ = O.nnls_update(Q, c[None, :], alpha, np.ones((1, 5)), O.nqp_opts(**CONVERGE))
+    np.testing.assert_allclose(X3[0], xs, rtol=1e-10, atol=1e-14)
+    assert X1[0].sum() > xs.sum()   # L1 shrinks
+
+
+def test_stop_rule_accelerated_condition():
+    A, B = WL.random_nqp(8, 30, rows=40)
+    Q = O.gram(A)
+    Cm = O.cross_dense(B, A)
+    X0 = WL.rng(1).random((40, 30))
+    for eps in (1e-1, 1e-3):
+        o = O.nqp_opts(max_inner=500, eps=eps)
+        for i in range(40):
+            h = -Cm[i]
+            x, k, s = O.nqp(Q, h, X0[i], o)
+            Qt, d, _ = O.rescale(Q)
+            y0 = X0[i] * d
+            g0 = Qt @ y0 + h / d
+            s0 = np.sum(np.where((y0 > 0) | (g0 < 0), g0, 0) ** 2)
+            assert k < 500 and s <= eps * s0
+
+
+# ----------------------------------------------------------------- outer loop
+def test_outer_objective_monotone_tiny():
+    for seed in range(3):
+        inst = WL.tiny(seed=seed, r=10)
+        W, Ht, hist, tot = O.nmf_solve(inst.W0, inst.Ht0, 50, V=inst.V,
+                                       opts=O.nqp_opts(max_inner=50, eps=1e-3))
+        J0 = O.objective_dense(inst.V, inst.W0, inst.Ht0)
+        seq = np.concatenate([[J0], hist])
+        assert np.all(np.diff(seq) <= 1e-12 * seq[:-1])
+        # the oracle's own history equals an independent numpy evaluation
+        ref = 0.5 * np.sum((inst.V - W @ Ht.T) ** 2)
+        assert abs(hist[-1] - ref) <= 1e-12 * ref
+        assert np.all(W >= 0) and np.all(Ht >= 0)
+
+
+def test_exact_low_rank_recovery():
+    ok = 0
+    for seed in range(5):
+        g = WL.rng(100 + seed)
+        W0 = g.random((60, 4))
+        H0 = g.random((4, 40))
+        V = W0 @ H0
+        W, Ht, hist, tot = O.nmf_solve(g.random((60, 4)), g.random((40, 4)), 400, V=V,
+                                       opts=O.nqp_opts(max_inner=100, eps=1e-6))
+        rel = np.linalg.norm(V - W @ Ht.T) / np.linalg.norm(V)
+        ok += rel <= 1e-3
+    assert ok >= 3
+
+
+def test_sparse_solve_equals_dense_solve():
+    rp, ci, va = WL.random_csr(12, 30, 25, 0.3, empty_rows=2)
+    m, n, r = 30, 25, 3
+    D = np.zeros((m, n))
+    for i in range(m):
+        D[i, ci[rp[i]:rp[i + 1]]] = va[rp[i]:rp[i + 1]]
+    trp, tci, tva = WL.csr_transpose(rp, ci, va, m, n)
+    g = WL.rng(4)
+    W0, H0 = g.random((m, r)), g.random((n, r))
+    o = O.nqp_opts(max_inner=10, eps=1e-4)
+    Wd, Hd, hd, td = O.nmf_solve(W0, H0, 8, V=D, alpha_h=0.01, opts=o)
+    Ws, Hs, hs, ts = O.nmf_solve(W0, H0, 8, csr=(rp, ci, va), csr_t=(trp, tci, tva),
+                                 alpha_h=0.01, opts=o)
+    np.testing.assert_allclose(Ws, Wd, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(hs, hd, rtol=1e-9)
+
+
+def test_maxstop_modes_reduce_inner_iterations():
+    inst = WL.tiny(seed=0, r=10)
+    tots = []
+    for mode in (0, 1, 2):
+        W, Ht, hist, tot = O.nmf_solve(inst.W0, inst.Ht0, 10, V=inst.V,
+                                       opts=O.nqp_opts(max_inner=50, eps=1e-3, maxstop_mode=mode))
+        tots.append(tot)
+        assert np.all(np.isfinite(hist))
+    assert tots[1] <= tots[0] and tots[2] <= tots[0]
+
+
+# ----------------------------------------------------------------- single steps of Alg. 3
+def _rescaled(H, h, x0):
+    d = np.sqrt(np.diag(H))
+    Qt = H / np.outer(d, d)
+    return Qt, h / d, x0 * d, d
+
+
+def test_one_projected_gradient_step_is_exact_line_search():
+    """max_inner=1 with no coordinate steps: y1 = [y0 - a g]_+ where a minimises
+    ft(y0 - a g) along the masked gradient (found numerically here)."""
+    so = pytest.importorskip("scipy.optimize")
+    g = WL.rng(31)
+    for r in (2, 5, 12):
+        for _ in range(5):
+            A = g.random((2 * r + 3, r))
+            H = A.T @ A
+            h = g.normal(size=r) * 3
+            x0 = g.random(r) * (g.random(r) > 0.3)
+            x1, k, s = O.nqp(H, h, x0, O.nqp_opts(max_inner=1, eps=0.0, cd_steps=0))
+            Qt, qt, y0, d = _rescaled(H, h, x0)
+            gr = Qt @ y0 + qt
+            gb = np.where((y0 > 0) | (gr < 0), gr, 0.0)
+            res = so.minimize_scalar(lambda a: 0.5 * (y0 - a * gb) @ Qt @ (y0 - a * gb)
+                                     + qt @ (y0 - a * gb), bounds=(0, 1e3), method="bounded",
+                                     options=dict(xatol=1e-13))
+            y1 = np.maximum(0, y0 - res.x * gb)
+            np.testing.assert_allclose(x1, y1 / d, rtol=1e-6, atol=1e-8)
+
+
+def test_one_coordinate_step_takes_largest_objective_decrease():
+    """cd_steps=1, no line search: the coordinate moved is the one whose exact
+    1-D minimisation lowers ft the most (evaluated by calling ft directly)."""
+    so = pytest.importorskip("scipy.optimize")
+    g = WL.rng(32)
+    for r in (3, 6, 10):
+        for _ in range(6):
+            A = g.random((2 * r + 3, r))
+            H = A.T @ A
+            h = g.normal(size=r) * 3
+            x0 = g.random(r) * (g.random(r) > 0.3)
+            x1, k, s = O.nqp(H, h, x0, O.nqp_opts(max_inner=1, eps=0.0, cd_steps=1, pg=0))
+            Qt, qt, y0, d = _rescaled(H, h, x0)
+
+            def ft(y):
+                return 0.5 * y @ Qt @ y + qt @ y
+
+            best, ybest = 0.0, y0
+            for i in range(r):
+                e = np.eye(r)[i]
+                res = so.minimize_scalar(lambda t: ft(y0 + t * e), bounds=(-y0[i], 1e3),
+                                         method="bounded", options=dict(xatol=1e-13))
+                dec = ft(y0) - ft(y0 + res.x * e)
+                if dec > best + 1e-9:
+                    best, ybest = dec, y0 + res.x * e
+            np.testing.assert_allclose(x1, ybest / d, rtol=1e-6, atol=1e-7)
+
+
+def test_stop_rule_stops_at_first_qualifying_iteration():
+    A, B = WL.random_nqp(18, 20, rows=15)
+    Q = O.gram(A)
+    Cm = O.cross_dense(B, A)
+    X0 = WL.rng(2).random((15, 20))
+    for eps in (1e-2, 1e-4):
+        for i in range(15):
+            x, k, s = O.nqp(Q, -Cm[i], X0[i], O.nqp_opts(max_inner=500, eps=eps))
+            Qt, qt, y0, d = _rescaled(Q, -Cm[i], X0[i])
+            g0 = Qt @ y0 + qt
+            s0 = np.sum(np.where((y0 > 0) | (g0 < 0), g0, 0) ** 2)
+            assert s <= eps * s0
+            if k > 1:
+                _, _, sp = O.nqp(Q, -Cm[i], X0[i], O.nqp_opts(max_inner=k - 1, eps=eps))
+                assert sp > eps * s0

@@ -1,0 +1,91 @@
+"""Mutation check of the oracle's pins.
+
+Each case plants one plausible mistake in a copy of ``oracle/oracle.c``
+(a dropped factor, a wrong sign or index, a missing penalty), builds it on the
+CPU, points the oracle module at the mutant and runs the pins of
+``test_oracle.py``: at least one pin must fail for every mutant.  The real
+oracle is never modified.
+"""
+import os
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle as O
+from tests import test_oracle as T
+
+SRC = os.path.join(os.path.dirname(O.__file__), "oracle.c")
+
+MUTANTS = {
+    "gain_drops_half": ("-(g[i] * di + 0.5 * qii * di * di)", "-(g[i] * di + qii * di * di)"),
+    "passive_set_drops_negative_grad": (
+        "gb[i] = (!dead[i] && (y[i] > 0.0 || g[i] < 0.0)) ? g[i] : 0.0;",
+        "gb[i] = (!dead[i] && (y[i] > 0.0)) ? g[i] : 0.0;"),
+    "pg_gradient_update_sign": ("            g[i] += t;\n", "            g[i] -= t;\n"),
+    "rescale_one_sided": ("H[i * r + j] / (d[i] * d[j])", "H[i * r + j] / d[i]"),
+    "linear_term_times_d": ("q[i] = dead[i] ? 0.0 : h[i] / d[i];", "q[i] = dead[i] ? 0.0 : h[i] * d[i];"),
+    "output_not_unscaled": ("x[i] = dead[i] ? 0.0 : y[i] / d[i];", "x[i] = dead[i] ? 0.0 : y[i];"),
+    "gram_drops_l2": ("Q[i * r + j] = s + (i == j ? beta : 0.0);", "Q[i * r + j] = s;"),
+    "row_drops_l1": ("h[j] = -C[i * r + j] + alpha;\n                double ms", "h[j] = -C[i * r + j];\n                double ms"),
+    "stop_rule_absolute": ("if (sk <= o->eps * s0)", "if (sk <= o->eps)"),
+    "cd_column_wrong": ("g[i] += Q[i * r + p] * dp;", "g[i] += Q[i * r + i] * dp;"),
+    "cross_index_swapped": ("s += A[i * lda + t] * B[t * r + j];", "s += A[i * lda + t] * B[j * r + t % r];"),
+    "tie_break_highest": ("if (gain > best) {", "if (gain >= best && gain > 0.0) {"),
+}
+
+PINS = [
+    T.test_worked_example_closed_form_and_59_steps,
+    lambda: T.test_nqp_matches_brute_force(4, 0.1, 0.05),
+    lambda: T.test_nqp_matches_brute_force(3, 0.3, 0.0),
+    T.test_nqp_matches_lawson_hanson,
+    T.test_rescale_invariants,
+    T.test_gram_and_cross_match_numpy,
+    T.test_penalties_enter_q_and_linear_term,
+    T.test_one_projected_gradient_step_is_exact_line_search,
+    T.test_one_coordinate_step_takes_largest_objective_decrease,
+    T.test_stop_rule_stops_at_first_qualifying_iteration,
+    T.test_diagonal_q_one_iteration_exact,
+    T.test_nqp_kkt_at_convergence,
+]
+
+
+def _tie_pin():
+    # equal gains on two coordinates: the lower index must move
+    import numpy as np
+    H = np.eye(3)
+    h = np.array([-1.0, -1.0, -0.5])
+    x, k, s = O.nqp(H, h, np.zeros(3), O.nqp_opts(max_inner=1, eps=0.0, cd_steps=1, pg=0))
+    assert x[0] == 1.0 and x[1] == 0.0
+
+
+PINS.append(_tie_pin)
+
+
+def test_tie_break_lowest_index():
+    _tie_pin()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_some_pin_catches_mutant(name, monkeypatch):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    tmp = tempfile.mkdtemp()
+    try:
+        path = os.path.join(tmp, "mut.c")
+        open(path, "w").write(src.replace(old, new, 1))
+        so = os.path.join(tmp, "libmut.so")
+        subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", so, path, "-lm"],
+                       check=True, capture_output=True)
+        monkeypatch.setattr(O, "_lib", O.load(so))
+        caught = 0
+        for pin in PINS:
+            try:
+                pin()
+            except AssertionError:
+                caught += 1
+        assert caught >= 1, f"no pin caught mutant {name}"
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
