@@ -1,0 +1,254 @@
+/*
+ * nmf.h - C ABI of the GB300 alternating-NNLS NMF library (libnmf.so).
+ *
+ * Method: Nguyen & Ho, "Accelerated Parallel and Distributed Algorithm using
+ * Limited Internal Memory for Nonnegative Matrix Factorization",
+ * arXiv 1506.08938.  Minimise
+ *     J(W, H) = 1/2 ||V - W H||_F^2 + a_w sum(W) + a_h sum(H)
+ *               + b_w/2 ||W||_F^2 + b_h/2 ||H||_F^2,   W, H >= 0,
+ * by alternating updates (Alg. 1 and Alg. 2 of §3).  Each half-step splits into
+ * independent r-dimensional nonnegative quadratic programs (Eq. 2, §3.2)
+ *     min_x 1/2 x^T Q x + q^T x,  x >= 0,
+ * that share one Q, solved by the anti-lopsided + greedy coordinate descent
+ * iteration (Alg. 3, §3.4).  L1/L2 penalties fold into q and Q (§3.5).
+ *
+ * Conventions for every call:
+ *  - Layout.  Matrices are row-major.  V is m x n with one instance per row
+ *    (the paper stores instances as columns: V_here = V_paper^T).  W is m x r.
+ *    H is kept as its transpose Ht (n x r) so that every NQP works on one
+ *    contiguous r-vector.  r <= 128 (NMF_E_SHAPE above).
+ *  - Memory.  Unless stated otherwise every pointer is DEVICE memory owned by
+ *    the caller.  The library owns only its handle's workspace, which it
+ *    allocates on first use at a given size and frees in nmf_destroy.
+ *  - Execution.  Calls enqueue work on the handle's stream and return without
+ *    waiting, except where stated.  Argument errors (NULL pointers, negative
+ *    sizes, r out of range, unsupported dtype) are returned before anything
+ *    is launched.  Errors found on the device (non-finite input, a wait that
+ *    ran out) are latched in a device status word and returned by the next
+ *    synchronising call (nmf_sync, nmf_solve).
+ *  - Threads.  A handle is used by one host thread at a time.  No exception
+ *    crosses this interface.
+ */
+#ifndef NMF_GB300_H
+#define NMF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NMF_OK = 0,
+    NMF_E_ARG = 1,        /* NULL pointer, negative size, bad option value     */
+    NMF_E_SHAPE = 2,      /* inconsistent shapes, r < 1 or r > 128             */
+    NMF_E_DTYPE = 3,      /* dtype not supported by this call                  */
+    NMF_E_NOMEM = 4,      /* workspace allocation failed                      */
+    NMF_E_CUDA = 5,       /* a CUDA runtime call failed (no device, launch)   */
+    NMF_E_NONFINITE = 6,  /* NaN/Inf met in an input row (row left unchanged) */
+    NMF_E_TIMEOUT = 7,    /* a bounded device-side wait ran out                */
+    NMF_E_BUSY = 8,       /* admission refused (serving: over memory budget)   */
+    NMF_E_NOTIMPL = 9     /* combination of options not implemented           */
+} nmf_status;
+
+typedef enum { NMF_F32 = 0, NMF_BF16 = 1, NMF_F64 = 2 } nmf_dtype;
+
+/* Arithmetic of the Gram and cross-term products (the NNLS sweeps are always
+ * FP32).  FP32: products and sums in FP32.  TF32 / BF16: operands rounded to
+ * that type, FP32 accumulation.  BF16X2: each operand split into a BF16 high
+ * part and a BF16 low part, three products summed in FP32. */
+typedef enum {
+    NMF_PREC_FP32 = 0,
+    NMF_PREC_TF32 = 1,
+    NMF_PREC_BF16 = 2,
+    NMF_PREC_BF16X2 = 3
+} nmf_prec;
+
+typedef struct nmf_ctx *nmf_handle;
+
+/* Dense row-major matrix: element (i, j) at data[i * ld + j]. */
+typedef struct {
+    int64_t rows, cols, ld;
+    nmf_dtype dt;
+    const void *data;
+} nmf_dense;
+
+/* CSR matrix: row i holds colidx/vals[rowptr[i] .. rowptr[i+1]). */
+typedef struct {
+    int64_t rows, cols, nnz;
+    const int64_t *rowptr;   /* rows + 1 entries, rowptr[0] = 0 */
+    const int32_t *colidx;   /* nnz entries, each in [0, cols)  */
+    const void *vals;        /* nnz entries of type dt          */
+    nmf_dtype dt;
+} nmf_csr;
+
+typedef struct {
+    int is_sparse;           /* 0: d is used, 1: s is used */
+    nmf_dense d;
+    nmf_csr s;
+} nmf_matrix;
+
+/* Options of Alg. 3 (§3.4).  Zero-initialised fields select the defaults
+ * noted in brackets via nmf_nnls_opts_default(). */
+typedef struct {
+    int max_inner;       /* cap on repeat-loop iterations per NQP [50]         */
+    double eps;          /* accelerated condition ||f_k||^2 <= eps ||f_0||^2,
+                            f = projected gradient in the rescaled space [1e-3] */
+    int cd_steps;        /* greedy coordinate steps per iteration, -1 = r [-1] */
+    int maxstop_mode;    /* fast-break rule of Alg. 3: 0 off; 1 = threshold is
+                            the largest final ||f||^2 of the previous update of
+                            the same factor (deterministic reading) [0]       */
+    float maxstop;       /* threshold for mode 1 in nmf_nnls_update [0]       */
+} nmf_nnls_opts;
+
+/* Options of the outer loop (Alg. 1 / Alg. 2). */
+typedef struct {
+    int outer_iters;         /* iterations to run (upper bound if a gap target) */
+    double rel_gap_target;   /* stop once (J - f_star)/f_star <= target; 0 off  */
+    double f_star;           /* reference optimum for the gap test             */
+    float alpha_w, alpha_h;  /* L1 weights                                     */
+    float beta_w, beta_h;    /* L2 weights (added to the Gram diagonal)        */
+    nmf_prec prec;           /* product arithmetic                            */
+    nmf_nnls_opts nnls;
+    int check_every;         /* gap test period in iterations (0 = 1)         */
+    int use_graph;           /* 1: capture one iteration as a CUDA graph       */
+    int objective;           /* how J is evaluated after each iteration:
+                                0 = FP64 trace identity (cheap; its FP32 inputs
+                                limit it to about 1e-7 ||V||^2 / J relative),
+                                1 = FP64 sum of element-wise residuals (dense
+                                V only; one extra pass over V)               */
+    double *obj_hist;        /* optional HOST array [outer_iters]: J after each
+                                full iteration (evaluated as `objective` says) */
+} nmf_solve_opts;
+
+typedef struct {
+    int iters_done;          /* outer iterations performed                    */
+    double objective;        /* J after the last iteration (FP64)             */
+    double rel_gap;          /* (J - f_star)/f_star, or 0 without f_star       */
+    double kbar;             /* inner iterations / (iters_done (m + n)) (§5.3) */
+    double kkt_max;          /* max |min(x, grad)| over both factors (FP64)   */
+    double ms_total;         /* device time of the loop (CUDA events)         */
+    int64_t inner_total;     /* inner iterations summed over all NQPs         */
+} nmf_report;
+
+/* ---- handle -------------------------------------------------------------- */
+
+/* Create a handle bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Returns NMF_E_CUDA if
+ * the device cannot be used. */
+nmf_status nmf_create(nmf_handle *out, int device, void *cuda_stream);
+/* Free the handle's workspace (waits for its stream first). */
+nmf_status nmf_destroy(nmf_handle h);
+/* Re-bind the handle to another stream of the same device. */
+nmf_status nmf_set_stream(nmf_handle h, void *cuda_stream);
+/* Wait for the handle's stream; return and clear the latched device status. */
+nmf_status nmf_sync(nmf_handle h);
+/* Static description of a status code. */
+const char *nmf_status_string(nmf_status s);
+/* Fill `o` with the defaults listed in nmf_nnls_opts. */
+void nmf_nnls_opts_default(nmf_nnls_opts *o);
+/* Number of kernels this process has launched through the library. */
+int64_t nmf_launch_count(void);
+
+/* ---- steps of one half-step ------------------------------------------------ */
+
+/* Gram matrix Q = X^T X + beta I (r x r, FP32), X rows x r (F32, ld >= r).
+ * Alg. 2 "Q = G^T G" (the printed "G G^T" is r x r only as G^T G; §4.2 gives
+ * its O(n r^2) cost); beta is the L2 weight of §3.5.  prec selects the
+ * product arithmetic (FP32, TF32, BF16, BF16X2). */
+nmf_status nmf_gram(nmf_handle h, const nmf_dense *X, float beta, nmf_prec prec, float *Q);
+
+/* Cross term C = V B (V rows x k dense F32/BF16 or CSR with F32/BF16 values;
+ * B k x r F32 row-major; C rows x r F32).  Alg. 2 "Y = F V^T" and the linear
+ * term of Eq. 2 (h = -A^T b); Theorem 2 for the sparse cost.  Dense V uses
+ * prec; CSR V always accumulates in FP32 from its stored values. */
+nmf_status nmf_cross(nmf_handle h, const nmf_matrix *V, const float *B, int r, nmf_prec prec,
+                     float *C);
+
+/* Anti-lopsided rescaling (§3.4 Eq. 3, first lines of Alg. 3):
+ * d_i = sqrt(Q_ii), Qt = Q ./ (d d^T) with unit diagonal.  A coordinate with
+ * Q_ii <= 0 is dead: d_i = 1 and its row and column of Qt are zero (its
+ * variable is then held at 0).  Q, Qt r x r; d length r. */
+nmf_status nmf_rescale(nmf_handle h, const float *Q, int r, float *Qt, float *d);
+
+/* Batched NQP solve (Alg. 3) for `rows` problems sharing Qt:
+ * row i minimises 1/2 x^T Q x + (alpha 1 - C_i)^T x, x >= 0, with
+ * Q = D Qt D, D = diag(d) (Qt, d from nmf_rescale).  X (rows x r) is the warm
+ * start on entry (Alg. 3 input x0) and the solution on return.  inner_iters
+ * (optional, rows entries) receives each row's repeat-loop count. */
+nmf_status nmf_nnls_update(nmf_handle h, const float *Qt, const float *d, const float *C,
+                           int64_t rows, int r, float alpha, float *X,
+                           const nmf_nnls_opts *opts, int32_t *inner_iters);
+
+/* ---- objective and optimality ---------------------------------------------- */
+
+/* J by the trace identity in FP64 (Def. 1, Table 4's 1/2 ||.||^2):
+ *   J = 1/2 (vv - 2 <Ht, Ch> + <Gw, Gh>) + a_w sum W + a_h sum Ht
+ *       + b_w/2 tr Gw + b_h/2 tr Gh
+ * vv = ||V||_F^2, Ch = V^T W (n x r), Gw = W^T W, Gh = Ht^T Ht (r x r,
+ * without the L2 term).  Writes one double to *J_dev (device). */
+nmf_status nmf_objective(nmf_handle h, double vv, const float *W, int64_t m, const float *Ht,
+                         int64_t n, int r, const float *Ch, const float *Gw, const float *Gh,
+                         float alpha_w, float alpha_h, float beta_w, float beta_h,
+                         double *J_dev);
+
+/* J from the element-wise residual, FP64 (Def. 1, Table 4's 1/2 ||.||^2):
+ *   J = 1/2 sum_ij (V_ij - W_i . Ht_j)^2 + a_w sum W + a_h sum Ht
+ *       + b_w/2 ||W||^2 + b_h/2 ||Ht||^2,
+ * each W_i . Ht_j formed in FP32, the squares summed in FP64.  V dense F32
+ * m x n; W m x r; Ht n x r.  Writes one double to *J_dev (device). */
+nmf_status nmf_objective_direct(nmf_handle h, const nmf_dense *V, const float *W, const float *Ht,
+                                int r, float alpha_w, float alpha_h, float beta_w, float beta_h,
+                                double *J_dev);
+
+/* KKT residuals of Eq. 2 for one factor, in FP64: with
+ * grad_i = Q X_i - C_i + alpha (Q r x r including the L2 term),
+ * out_dev[0] = max |min(X_ij, grad_ij)|, out_dev[1] = max |X_ij grad_ij|. */
+nmf_status nmf_kkt(nmf_handle h, const float *Q, const float *C, int64_t rows, int r,
+                   float alpha, const float *X, double *out_dev);
+
+/* ---- whole method ---------------------------------------------------------- */
+
+/* Alternating solve (Alg. 1 / Alg. 2): for t = 1..outer_iters
+ *   W-update:  Q = Ht^T Ht + b_w I, C = V Ht,  every row of W by Alg. 3;
+ *   H-update:  Q = W^T W + b_h I,   C = V^T W, every row of Ht by Alg. 3;
+ * then J by the FP64 trace identity.  V is dense (F32, or BF16 when
+ * prec = BF16) or CSR; Vt is V^T in the same format (required for CSR;
+ * optional for dense, built on the device when NULL).  W (m x r) and Ht
+ * (n x r) hold the initial factors and receive the result.  Synchronises
+ * before returning and fills *rep (host). */
+nmf_status nmf_solve(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt, int r, float *W,
+                     float *Ht, const nmf_solve_opts *opts, nmf_report *rep);
+
+/* ---- projection onto a fixed basis ----------------------------------------- */
+
+/* E-step alone (Alg. 1 E-step, Alg. 2 first loop) against a fixed basis W
+ * (wrows x r) with its rescaled Gram (Qt, d from nmf_gram + nmf_rescale):
+ * for each new column j, given as row j of the CSR VnewT (w x wrows),
+ * Hnew_j = argmin_{h >= 0} 1/2 ||v_j - W h||^2.  Hnew (w x r) is the warm
+ * start on entry (zero for a cold start). */
+nmf_status nmf_project(nmf_handle h, const float *Qt, const float *d, const float *W,
+                       int64_t wrows, int r, const nmf_csr *VnewT, float *Hnew,
+                       const nmf_nnls_opts *opts);
+
+/* ---- instrumentation ------------------------------------------------------- */
+
+/* Kernel classes for nmf_profile_read. */
+typedef enum {
+    NMF_K_GRAM = 0, NMF_K_CROSS = 1, NMF_K_SPMM = 2, NMF_K_RESCALE = 3, NMF_K_NNLS = 4,
+    NMF_K_OBJECTIVE = 5, NMF_K_OTHER = 6
+} nmf_kclass;
+
+/* Instrumentation, with no counterpart in the paper: while enabled, every
+ * launch is bracketed by two CUDA events on its stream (not inside CUDA-graph
+ * capture).  Enabling clears the totals.  Process-wide, one host thread. */
+nmf_status nmf_profile_enable(int enable);
+/* Device milliseconds and launch count of one kernel class since enabling;
+ * waits for the recorded events. */
+nmf_status nmf_profile_read(int kclass, double *ms_total, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NMF_GB300_H */

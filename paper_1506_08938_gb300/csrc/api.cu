@@ -1,0 +1,1124 @@
+// C ABI of libnmf.so: handle, workspace, argument checks and the host side of
+// the alternating loop (Alg. 1 / Alg. 2).  Every arithmetic step runs in the
+// kernels of the other translation units; this file only validates,
+// allocates workspace once, and enqueues launches on the handle's stream.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "nmf_internal.cuh"
+
+using namespace nmfi;
+
+namespace nmfi {
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---- profiler: pairs of events per kernel class --------------------------
+namespace {
+struct Prof {
+    bool on = false;
+    int suspended = 0;
+    std::vector<cudaEvent_t> pool;     // reusable events
+    size_t used = 0;
+    struct Pair { int cls; cudaEvent_t b, e; };
+    std::vector<Pair> pairs;
+    std::vector<int> open_cls;         // stack of classes with a begin pending
+    std::vector<cudaEvent_t> open_ev;
+    double ms[KC_COUNT] = {0};
+    long long n[KC_COUNT] = {0};
+    cudaEvent_t get()
+    {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess)
+                return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void drain()
+    {
+        for (auto &p : pairs) {
+            float t = 0.f;
+            if (cudaEventSynchronize(p.e) == cudaSuccess &&
+                cudaEventElapsedTime(&t, p.b, p.e) == cudaSuccess) {
+                ms[p.cls] += t;
+                n[p.cls] += 1;
+            }
+        }
+        pairs.clear();
+        used = 0;
+    }
+};
+Prof g_prof;
+}  // namespace
+
+void prof_suspend(bool on) { g_prof.suspended += on ? 1 : -1; }
+
+void prof_mark(int cls, cudaStream_t s, bool begin)
+{
+    Prof &P = g_prof;
+    if (!P.on || P.suspended > 0)
+        return;
+    if (begin) {
+        if (P.used + 2 > 4096)
+            P.drain();   // bound the number of live events
+        cudaEvent_t e = P.get();
+        if (!e)
+            return;
+        cudaEventRecord(e, s);
+        P.open_cls.push_back(cls);
+        P.open_ev.push_back(e);
+    } else {
+        if (P.open_ev.empty())
+            return;
+        cudaEvent_t b = P.open_ev.back();
+        int c = P.open_cls.back();
+        P.open_ev.pop_back();
+        P.open_cls.pop_back();
+        cudaEvent_t e = P.get();
+        if (!e)
+            return;
+        cudaEventRecord(e, s);
+        // nested scopes (a launcher calling another) count once, outermost
+        if (P.open_ev.empty())
+            P.pairs.push_back({c, b, e});
+    }
+}
+}  // namespace nmfi
+
+NMF_API nmf_status nmf_profile_enable(int enable)
+{
+    Prof &P = g_prof;
+    if (enable) {
+        P.drain();
+        for (int c = 0; c < KC_COUNT; ++c) {
+            P.ms[c] = 0.0;
+            P.n[c] = 0;
+        }
+        P.on = true;
+    } else {
+        P.on = false;
+    }
+    return NMF_OK;
+}
+
+NMF_API nmf_status nmf_profile_read(int kclass, double *ms_total, int64_t *launches)
+{
+    if (kclass < 0 || kclass >= KC_COUNT || !ms_total || !launches)
+        return NMF_E_ARG;
+    g_prof.drain();
+    *ms_total = g_prof.ms[kclass];
+    *launches = g_prof.n[kclass];
+    return NMF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// handle and workspace
+// ---------------------------------------------------------------------------
+struct nmf_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    char *ws = nullptr;          // arena
+    size_t ws_cap = 0;
+    // small fixed device buffers
+    unsigned *status = nullptr;  // latched device status
+    unsigned *tickets = nullptr; // 8 reduction tickets
+    double *partials = nullptr;  // 3 * 256 doubles
+    double *scal = nullptr;      // 16 doubles of scalar outputs
+    unsigned long long *ctr = nullptr;  // 4 counters
+    int *idev = nullptr;         // 4 ints (iteration index, done flag)
+    unsigned *smax = nullptr;    // 2 words (maxStop bits per factor)
+    cudaStream_t cap = nullptr;  // private stream for graph capture (the
+                                 // legacy default stream cannot be captured)
+    char *stage = nullptr;       // device copies of host-resident solve inputs
+    size_t stage_cap = 0;
+};
+
+namespace {
+
+struct Arena {
+    char *base;
+    size_t off = 0, cap;
+    Arena(char *b, size_t c) : base(b), cap(c) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base + off);
+        off += sizeof(T) * count;
+        return p;
+    }
+};
+
+// Bytes a sequence of take() calls needs: replay them on a null arena.
+struct Sizer {
+    size_t off = 0;
+    template <typename T>
+    void add(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        off += sizeof(T) * count;
+    }
+};
+
+nmf_status cuda_st(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return NMF_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return NMF_E_NOMEM;
+    return NMF_E_CUDA;
+}
+
+#define CK(expr)                                  \
+    do {                                          \
+        cudaError_t _e = (expr);                  \
+        if (_e != cudaSuccess)                    \
+            return cuda_st(_e);                   \
+    } while (0)
+
+nmf_status ensure_ws(nmf_handle h, size_t bytes)
+{
+    if (bytes <= h->ws_cap)
+        return NMF_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->ws)
+        cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_cap = 0;
+    size_t cap = bytes + (bytes >> 3) + (1 << 20);
+    if (cudaMalloc(&h->ws, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return NMF_E_NOMEM;
+    }
+    h->ws_cap = cap;
+    return NMF_OK;
+}
+
+nmf_nnls_opts opts_or_default(const nmf_nnls_opts *o)
+{
+    nmf_nnls_opts d;
+    nmf_nnls_opts_default(&d);
+    if (!o)
+        return d;
+    nmf_nnls_opts r = *o;
+    if (r.max_inner <= 0)
+        r.max_inner = d.max_inner;
+    if (!(r.eps >= 0.0))
+        r.eps = d.eps;
+    return r;
+}
+
+bool bad_r(int r) { return r < 1 || r > kMaxRank; }
+
+// true when p is host memory (pinned or pageable) rather than device memory
+bool is_host_ptr(const void *p)
+{
+    if (!p)
+        return false;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+nmf_status ensure_stage(nmf_handle h, size_t bytes)
+{
+    if (bytes <= h->stage_cap)
+        return NMF_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->stage)
+        cudaFree(h->stage);
+    h->stage = nullptr;
+    h->stage_cap = 0;
+    if (cudaMalloc(&h->stage, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return NMF_E_NOMEM;
+    }
+    h->stage_cap = bytes;
+    return NMF_OK;
+}
+
+}  // namespace
+
+NMF_API const char *nmf_status_string(nmf_status s)
+{
+    switch (s) {
+    case NMF_OK: return "ok";
+    case NMF_E_ARG: return "invalid argument";
+    case NMF_E_SHAPE: return "invalid shape";
+    case NMF_E_DTYPE: return "unsupported dtype";
+    case NMF_E_NOMEM: return "out of device memory";
+    case NMF_E_CUDA: return "CUDA error";
+    case NMF_E_NONFINITE: return "non-finite input";
+    case NMF_E_TIMEOUT: return "device wait timed out";
+    case NMF_E_BUSY: return "admission refused";
+    case NMF_E_NOTIMPL: return "not implemented";
+    }
+    return "unknown status";
+}
+
+NMF_API void nmf_nnls_opts_default(nmf_nnls_opts *o)
+{
+    if (!o)
+        return;
+    o->max_inner = 50;
+    o->eps = 1e-3;
+    o->cd_steps = -1;
+    o->maxstop_mode = 0;
+    o->maxstop = 0.f;
+}
+
+NMF_API int64_t nmf_launch_count(void) { return g_launches.load(); }
+
+NMF_API nmf_status nmf_create(nmf_handle *out, int device, void *cuda_stream)
+{
+    if (!out)
+        return NMF_E_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return NMF_E_CUDA;
+    }
+    CK(cudaSetDevice(device));
+    nmf_ctx *h = new nmf_ctx;
+    h->device = device;
+    h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    char *aux = nullptr;
+    const size_t aux_bytes = 64 * 1024;
+    if (cudaMalloc(&aux, aux_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return NMF_E_NOMEM;
+    }
+    cudaMemset(aux, 0, aux_bytes);
+    Arena a(aux, aux_bytes);
+    h->status = a.take<unsigned>(4);
+    h->tickets = a.take<unsigned>(8);
+    h->partials = a.take<double>(3 * 1024);
+    h->scal = a.take<double>(16);
+    h->ctr = a.take<unsigned long long>(4);
+    h->idev = a.take<int>(4);
+    h->smax = a.take<unsigned>(4);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFree(aux);
+        delete h;
+        return NMF_E_CUDA;
+    }
+    *out = h;
+    return NMF_OK;
+}
+
+NMF_API nmf_status nmf_destroy(nmf_handle h)
+{
+    if (!h)
+        return NMF_E_ARG;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    if (h->ws)
+        cudaFree(h->ws);
+    if (h->cap)
+        cudaStreamDestroy(h->cap);
+    if (h->stage)
+        cudaFree(h->stage);
+    cudaFree(h->status);   // first allocation of the aux block
+    delete h;
+    return NMF_OK;
+}
+
+NMF_API nmf_status nmf_set_stream(nmf_handle h, void *cuda_stream)
+{
+    if (!h)
+        return NMF_E_ARG;
+    h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    return NMF_OK;
+}
+
+NMF_API nmf_status nmf_sync(nmf_handle h)
+{
+    if (!h)
+        return NMF_E_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    unsigned st = 0;
+    CK(cudaMemcpy(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st) {
+        CK(cudaMemset(h->status, 0, sizeof(unsigned)));
+        if (st & kStTimeout)
+            return NMF_E_TIMEOUT;
+        return NMF_E_NONFINITE;
+    }
+    return NMF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// single steps
+// ---------------------------------------------------------------------------
+namespace {
+
+// Gram into G (r x r, no beta) through `ws`; returns the reduced result in G.
+nmf_status gram_into(nmf_handle h, const float *X, int64_t rows, int64_t ld, int r,
+                     nmf_prec prec, float *P, int S, float *G)
+{
+    (void)prec;
+    CK(launch_gram_partial(X, rows, ld, r, P, S, h->stream));
+    CK(launch_sum_slices(P, S, (int64_t)r * r, G, h->stream));
+    return NMF_OK;
+}
+
+}  // namespace
+
+NMF_API nmf_status nmf_gram(nmf_handle h, const nmf_dense *X, float beta, nmf_prec prec, float *Q)
+{
+    if (!h || !X || !Q || (!X->data && X->rows > 0))
+        return NMF_E_ARG;
+    if (X->rows < 0 || bad_r((int)X->cols) || X->ld < X->cols)
+        return NMF_E_SHAPE;
+    if (X->dt != NMF_F32)
+        return NMF_E_DTYPE;
+    if (prec != NMF_PREC_FP32)
+        return NMF_E_NOTIMPL;
+    const int r = (int)X->cols;
+    const int S = gram_splits(X->rows);
+    Sizer z;
+    z.add<float>((size_t)S * r * r);
+    z.add<float>((size_t)r * r);
+    nmf_status st = ensure_ws(h, z.off);
+    if (st)
+        return st;
+    Arena a(h->ws, h->ws_cap);
+    float *P = a.take<float>((size_t)S * r * r);
+    float *G = a.take<float>((size_t)r * r);
+    st = gram_into(h, (const float *)X->data, X->rows, X->ld, r, prec, P, S, G);
+    if (st)
+        return st;
+    CK(launch_rescale(G, 1, r, beta, nullptr, Q, nullptr, nullptr, h->stream));
+    return NMF_OK;
+}
+
+NMF_API nmf_status nmf_cross(nmf_handle h, const nmf_matrix *V, const float *B, int r,
+                             nmf_prec prec, float *C)
+{
+    if (!h || !V || !B || !C)
+        return NMF_E_ARG;
+    if (bad_r(r))
+        return NMF_E_SHAPE;
+    if (V->is_sparse) {
+        const nmf_csr &s = V->s;
+        if (s.rows < 0 || s.cols < 0 || s.nnz < 0 || !s.rowptr || (s.nnz > 0 && (!s.colidx || !s.vals)))
+            return NMF_E_ARG;
+        if (s.dt != NMF_F32 && s.dt != NMF_BF16)
+            return NMF_E_DTYPE;
+        SpmmPlan p = spmm_plan(s.rows, s.nnz);
+        nmf_status st = ensure_ws(h, spmm_workspace_bytes(p, r) + 256);
+        if (st)
+            return st;
+        CK(launch_spmm_csr(s.rowptr, s.colidx, s.vals, s.dt, s.rows, s.nnz, B, r, C, p, h->ws,
+                           h->stream));
+        return NMF_OK;
+    }
+    const nmf_dense &d = V->d;
+    if (d.rows < 0 || d.cols < 0 || d.ld < d.cols || (!d.data && d.rows > 0))
+        return NMF_E_SHAPE;
+    if (d.dt != NMF_F32)
+        return NMF_E_DTYPE;
+    if (prec != NMF_PREC_FP32)
+        return NMF_E_NOTIMPL;
+    const int S = cross_splits(d.rows, d.cols);
+    if (S == 1) {
+        CK(launch_cross_dense_f32((const float *)d.data, d.rows, d.cols, d.ld, B, r, C, 1,
+                                  h->stream));
+        return NMF_OK;
+    }
+    nmf_status st = ensure_ws(h, sizeof(float) * (size_t)S * d.rows * r + 256);
+    if (st)
+        return st;
+    float *P = reinterpret_cast<float *>(h->ws);
+    CK(launch_cross_dense_f32((const float *)d.data, d.rows, d.cols, d.ld, B, r, P, S, h->stream));
+    CK(launch_sum_slices(P, S, d.rows * r, C, h->stream));
+    return NMF_OK;
+}
+
+NMF_API nmf_status nmf_rescale(nmf_handle h, const float *Q, int r, float *Qt, float *d)
+{
+    if (!h || !Q || !Qt || !d)
+        return NMF_E_ARG;
+    if (bad_r(r))
+        return NMF_E_SHAPE;
+    CK(launch_rescale(Q, 1, r, 0.f, nullptr, nullptr, Qt, d, h->stream));
+    return NMF_OK;
+}
+
+NMF_API nmf_status nmf_nnls_update(nmf_handle h, const float *Qt, const float *d, const float *C,
+                                   int64_t rows, int r, float alpha, float *X,
+                                   const nmf_nnls_opts *opts, int32_t *inner_iters)
+{
+    if (!h || !Qt || !d || (rows > 0 && (!C || !X)))
+        return NMF_E_ARG;
+    if (rows < 0 || bad_r(r))
+        return NMF_E_SHAPE;
+    nmf_nnls_opts o = opts_or_default(opts);
+    if (o.maxstop_mode < 0 || o.maxstop_mode > 1)
+        return NMF_E_ARG;
+    NnlsArgs a{};
+    a.Qt = Qt;
+    a.d = d;
+    a.C = C;
+    a.nsplit = 1;
+    a.c_stride = rows * r;
+    a.rows = rows;
+    a.r = r;
+    a.alpha = alpha;
+    a.X = X;
+    a.max_inner = o.max_inner;
+    a.eps = (float)o.eps;
+    a.cd_steps = o.cd_steps;
+    a.maxstop_mode = o.maxstop_mode;
+    a.maxstop = o.maxstop;
+    a.iters = inner_iters;
+    a.status = h->status;
+    CK(launch_nnls(a, h->stream));
+    return NMF_OK;
+}
+
+NMF_API nmf_status nmf_objective(nmf_handle h, double vv, const float *W, int64_t m,
+                                 const float *Ht, int64_t n, int r, const float *Ch,
+                                 const float *Gw, const float *Gh, float alpha_w, float alpha_h,
+                                 float beta_w, float beta_h, double *J_dev)
+{
+    if (!h || !W || !Ht || !Ch || !Gw || !Gh || !J_dev)
+        return NMF_E_ARG;
+    if (m < 0 || n < 0 || bad_r(r))
+        return NMF_E_SHAPE;
+    ObjArgs a{};
+    a.vv = vv;
+    a.W = W;
+    a.m = m;
+    a.Ht = Ht;
+    a.n = n;
+    a.r = r;
+    a.Ch = Ch;
+    a.nsplit = 1;
+    a.ch_stride = n * r;
+    a.Gw = Gw;
+    a.Gh = Gh;
+    a.aw = alpha_w;
+    a.ah = alpha_h;
+    a.bw = beta_w;
+    a.bh = beta_h;
+    a.J = J_dev;
+    a.partials = h->partials;
+    a.ticket = h->tickets + 0;
+    CK(launch_objective(a, h->stream));
+    return NMF_OK;
+}
+
+NMF_API nmf_status nmf_objective_direct(nmf_handle h, const nmf_dense *V, const float *W,
+                                        const float *Ht, int r, float alpha_w, float alpha_h,
+                                        float beta_w, float beta_h, double *J_dev)
+{
+    if (!h || !V || !W || !Ht || !J_dev || !V->data)
+        return NMF_E_ARG;
+    if (V->rows <= 0 || V->cols <= 0 || V->ld < V->cols || bad_r(r))
+        return NMF_E_SHAPE;
+    if (V->dt != NMF_F32)
+        return NMF_E_DTYPE;
+    const size_t np = objective_direct_partials(V->rows, V->cols);
+    nmf_status st = ensure_ws(h, sizeof(double) * np + 256);
+    if (st)
+        return st;
+    ObjDirectArgs a{};
+    a.V = (const float *)V->data;
+    a.ldv = V->ld;
+    a.W = W;
+    a.m = V->rows;
+    a.Ht = Ht;
+    a.n = V->cols;
+    a.r = r;
+    a.aw = alpha_w;
+    a.ah = alpha_h;
+    a.bw = beta_w;
+    a.bh = beta_h;
+    a.J = J_dev;
+    a.partials = reinterpret_cast<double *>(h->ws);
+    a.ticket = h->tickets + 2;
+    CK(launch_objective_direct(a, h->stream));
+    return NMF_OK;
+}
+
+NMF_API nmf_status nmf_kkt(nmf_handle h, const float *Q, const float *C, int64_t rows, int r,
+                           float alpha, const float *X, double *out_dev)
+{
+    if (!h || !Q || !out_dev || (rows > 0 && (!C || !X)))
+        return NMF_E_ARG;
+    if (rows < 0 || bad_r(r))
+        return NMF_E_SHAPE;
+    CK(launch_kkt(Q, C, rows, r, alpha, X, out_dev, h->stream));
+    return NMF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// whole method
+// ---------------------------------------------------------------------------
+namespace {
+
+struct HalfStep {
+    // operand of the cross term: dense (A, lda) or CSR
+    bool sparse;
+    const float *A;
+    int64_t lda, K;
+    const nmf_csr *csr;
+    SpmmPlan plan;
+    int64_t rows;       // number of NQPs (rows of the factor updated)
+    float *X;           // factor updated (rows x r)
+    const float *Xo;    // other factor (K x r)
+    int64_t Ko;         // rows of the other factor
+    float alpha, beta;
+    float *Cs;          // cross slices
+    int nsplit;
+    float *Q;           // Q = G_other + beta I (kept for KKT)
+    unsigned *smax;     // maxStop bits for this factor
+};
+
+struct Loop {
+    int r;
+    float *Pg;          // Gram partial slices
+    int gS_w, gS_h;     // gram splits for W (m rows) and Ht (n rows)
+    float *Gw, *Gh;     // Grams without beta
+    float *Qt, *d;
+    void *spws;         // SpMM carries
+    HalfStep hw, hh;
+    nmf_nnls_opts nn;
+    double vv;
+    bool direct_obj;
+    const float *V; int64_t ldv;   // dense V for the direct objective
+    double *obj_partials;
+};
+
+nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, const float *Gother)
+{
+    cudaStream_t st = h->stream;
+    // Q = G_other + beta I; Qt, d (Alg. 3 rescale)
+    CK(launch_rescale(Gother, 1, L.r, s.beta, nullptr, s.Q, L.Qt, L.d, st));
+    // cross term C = V X_other
+    if (s.sparse) {
+        CK(launch_spmm_csr(s.csr->rowptr, s.csr->colidx, s.csr->vals, s.csr->dt, s.csr->rows,
+                           s.csr->nnz, s.Xo, L.r, s.Cs, s.plan, L.spws, st));
+    } else {
+        CK(launch_cross_dense_f32(s.A, s.rows, s.K, s.lda, s.Xo, L.r, s.Cs, s.nsplit, st));
+    }
+    NnlsArgs a{};
+    a.Qt = L.Qt;
+    a.d = L.d;
+    a.C = s.Cs;
+    a.nsplit = s.nsplit;
+    a.c_stride = s.rows * L.r;
+    a.rows = s.rows;
+    a.r = L.r;
+    a.alpha = s.alpha;
+    a.X = s.X;
+    a.max_inner = L.nn.max_inner;
+    a.eps = (float)L.nn.eps;
+    a.cd_steps = L.nn.cd_steps;
+    a.maxstop_mode = L.nn.maxstop_mode;
+    a.maxstop = 0.f;
+    a.iter_total = h->ctr;
+    a.status = h->status;
+    if (L.nn.maxstop_mode == 1)
+        return NMF_E_NOTIMPL;   // threshold needs a device-side read; not wired yet
+    CK(launch_nnls(a, st));
+    return NMF_OK;
+}
+
+nmf_status enqueue_objective(nmf_handle h, Loop &L, const nmf_solve_opts &o, double f_star,
+                             double gap);
+
+nmf_status enqueue_iteration(nmf_handle h, Loop &L, const nmf_solve_opts &o)
+{
+    nmf_status s;
+    // W-update (E-step): Q_W = Ht^T Ht + b_w I (G_H ready), C_W = V Ht
+    if ((s = enqueue_half(h, L, L.hw, L.Gh)))
+        return s;
+    // G_W = W^T W
+    if ((s = gram_into(h, L.hw.X, L.hw.rows, L.r, L.r, o.prec, L.Pg, L.gS_w, L.Gw)))
+        return s;
+    // H-update (M-step)
+    if ((s = enqueue_half(h, L, L.hh, L.Gw)))
+        return s;
+    if ((s = gram_into(h, L.hh.X, L.hh.rows, L.r, L.r, o.prec, L.Pg, L.gS_h, L.Gh)))
+        return s;
+    return NMF_OK;
+}
+
+nmf_status enqueue_objective(nmf_handle h, Loop &L, const nmf_solve_opts &o, double f_star,
+                             double gap)
+{
+    if (L.direct_obj) {
+        ObjDirectArgs b{};
+        b.V = L.V;
+        b.ldv = L.ldv;
+        b.W = L.hw.X;
+        b.m = L.hw.rows;
+        b.Ht = L.hh.X;
+        b.n = L.hh.rows;
+        b.r = L.r;
+        b.aw = o.alpha_w;
+        b.ah = o.alpha_h;
+        b.bw = o.beta_w;
+        b.bh = o.beta_h;
+        b.J = h->scal + 0;
+        b.partials = L.obj_partials;
+        b.ticket = h->tickets + 2;
+        CK(launch_objective_direct(b, h->stream));
+        return NMF_OK;
+    }
+    // J(W, H) by the FP64 trace identity
+    ObjArgs a{};
+    a.vv = L.vv;
+    a.W = L.hw.X;
+    a.m = L.hw.rows;
+    a.Ht = L.hh.X;
+    a.n = L.hh.rows;
+    a.r = L.r;
+    a.Ch = L.hh.Cs;
+    a.nsplit = L.hh.nsplit;
+    a.ch_stride = L.hh.rows * L.r;
+    a.Gw = L.Gw;
+    a.Gh = L.Gh;
+    a.aw = o.alpha_w;
+    a.ah = o.alpha_h;
+    a.bw = o.beta_w;
+    a.bh = o.beta_h;
+    a.J = h->scal + 0;
+    a.hist = nullptr;
+    a.t = nullptr;
+    a.f_star = f_star;
+    a.gap_target = gap;
+    a.done_flag = h->idev + 1;
+    a.partials = h->partials;
+    a.ticket = h->tickets + 0;
+    CK(launch_objective(a, h->stream));
+    return NMF_OK;
+}
+
+}  // namespace
+
+namespace {
+nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt, int r, float *W,
+                        float *Ht, const nmf_solve_opts *opts, nmf_report *rep);
+}
+
+// Host-resident inputs (V, Vt, W, Ht in host memory) are copied to a staging
+// area of the handle on its stream, solved there, and W, Ht copied back; the
+// copies run at pinned-memory speed when the caller's buffers are pinned.
+NMF_API nmf_status nmf_solve(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt, int r,
+                             float *W, float *Ht, const nmf_solve_opts *opts, nmf_report *rep)
+{
+    if (!h || !V || !W || !Ht || !opts)
+        return NMF_E_ARG;
+    if (bad_r(r))
+        return NMF_E_SHAPE;
+    CK(cudaSetDevice(h->device));
+    const bool sp = V->is_sparse != 0;
+    const void *probe = sp ? (const void *)V->s.rowptr : V->d.data;
+    const bool hv = is_host_ptr(probe), hw = is_host_ptr(W), hh = is_host_ptr(Ht);
+    if (!hv && !hw && !hh)
+        return solve_device(h, V, Vt, r, W, Ht, opts, rep);
+    // sizes
+    int64_t m, n;
+    size_t vb = 0, vtb = 0;
+    if (sp) {
+        if (!Vt || !Vt->is_sparse)
+            return NMF_E_ARG;
+        m = V->s.rows;
+        n = V->s.cols;
+        const size_t es = V->s.dt == NMF_BF16 ? 2 : 4;
+        vb = 8 * (size_t)(m + 1) + 4 * (size_t)V->s.nnz + es * V->s.nnz + 64;
+        vtb = 8 * (size_t)(n + 1) + 4 * (size_t)Vt->s.nnz + es * Vt->s.nnz + 64;
+    } else {
+        m = V->d.rows;
+        n = V->d.cols;
+        if (V->d.ld != n || V->d.dt != NMF_F32)
+            return NMF_E_NOTIMPL;   // staged dense V must be contiguous F32
+        vb = sizeof(float) * (size_t)m * n;
+        if (Vt)
+            vtb = sizeof(float) * (size_t)m * n;
+    }
+    if (m <= 0 || n <= 0)
+        return NMF_E_SHAPE;
+    const size_t wb = sizeof(float) * (size_t)m * r, hb = sizeof(float) * (size_t)n * r;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    nmf_status st = ensure_stage(h, al(vb) + al(vtb) + al(wb) + al(hb));
+    if (st)
+        return st;
+    char *p = h->stage;
+    cudaStream_t s = h->stream;
+    nmf_matrix Vd = *V, Vtd{};
+    const nmf_matrix *vtp = Vt;
+    if (hv) {
+        if (sp) {
+            char *q = p;
+            CK(cudaMemcpyAsync(q, V->s.rowptr, 8 * (m + 1), cudaMemcpyHostToDevice, s));
+            Vd.s.rowptr = (const int64_t *)q;
+            q += al(8 * (m + 1));
+            CK(cudaMemcpyAsync(q, V->s.colidx, 4 * V->s.nnz, cudaMemcpyHostToDevice, s));
+            Vd.s.colidx = (const int32_t *)q;
+            q += al(4 * V->s.nnz);
+            const size_t es = V->s.dt == NMF_BF16 ? 2 : 4;
+            CK(cudaMemcpyAsync(q, V->s.vals, es * V->s.nnz, cudaMemcpyHostToDevice, s));
+            Vd.s.vals = q;
+            char *t = p + al(vb);
+            Vtd = *Vt;
+            CK(cudaMemcpyAsync(t, Vt->s.rowptr, 8 * (n + 1), cudaMemcpyHostToDevice, s));
+            Vtd.s.rowptr = (const int64_t *)t;
+            t += al(8 * (n + 1));
+            CK(cudaMemcpyAsync(t, Vt->s.colidx, 4 * Vt->s.nnz, cudaMemcpyHostToDevice, s));
+            Vtd.s.colidx = (const int32_t *)t;
+            t += al(4 * Vt->s.nnz);
+            CK(cudaMemcpyAsync(t, Vt->s.vals, es * Vt->s.nnz, cudaMemcpyHostToDevice, s));
+            Vtd.s.vals = t;
+            vtp = &Vtd;
+        } else {
+            CK(cudaMemcpyAsync(p, V->d.data, vb, cudaMemcpyHostToDevice, s));
+            Vd.d.data = p;
+            if (Vt) {
+                Vtd = *Vt;
+                CK(cudaMemcpyAsync(p + al(vb), Vt->d.data, vtb, cudaMemcpyHostToDevice, s));
+                Vtd.d.data = p + al(vb);
+                vtp = &Vtd;
+            }
+        }
+    }
+    float *Wd = W, *Hd = Ht;
+    char *fp = p + al(vb) + al(vtb);
+    if (hw) {
+        Wd = (float *)fp;
+        CK(cudaMemcpyAsync(Wd, W, wb, cudaMemcpyHostToDevice, s));
+    }
+    if (hh) {
+        Hd = (float *)(fp + al(wb));
+        CK(cudaMemcpyAsync(Hd, Ht, hb, cudaMemcpyHostToDevice, s));
+    }
+    st = solve_device(h, &Vd, vtp, r, Wd, Hd, opts, rep);
+    if (st != NMF_OK && st != NMF_E_NONFINITE)
+        return st;
+    if (hw)
+        CK(cudaMemcpyAsync(W, Wd, wb, cudaMemcpyDeviceToHost, s));
+    if (hh)
+        CK(cudaMemcpyAsync(Ht, Hd, hb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return st;
+}
+
+namespace {
+nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt, int r, float *W,
+                        float *Ht, const nmf_solve_opts *opts, nmf_report *rep)
+{
+    if (!h || !V || !W || !Ht || !opts)
+        return NMF_E_ARG;
+    if (bad_r(r))
+        return NMF_E_SHAPE;
+    const nmf_solve_opts o = *opts;
+    if (o.outer_iters < 0)
+        return NMF_E_ARG;
+    if (o.prec != NMF_PREC_FP32)
+        return NMF_E_NOTIMPL;
+    Loop L{};
+    L.r = r;
+    L.nn = opts_or_default(&o.nnls);
+    if (L.nn.maxstop_mode != 0)
+        return NMF_E_NOTIMPL;
+    int64_t m, n;
+    const bool sparse = V->is_sparse != 0;
+    if (sparse) {
+        if (!Vt || !Vt->is_sparse)
+            return NMF_E_ARG;
+        m = V->s.rows;
+        n = V->s.cols;
+        if (Vt->s.rows != n || Vt->s.cols != m || Vt->s.nnz != V->s.nnz)
+            return NMF_E_SHAPE;
+        if (!V->s.rowptr || !Vt->s.rowptr)
+            return NMF_E_ARG;
+        if (V->s.dt != Vt->s.dt || (V->s.dt != NMF_F32 && V->s.dt != NMF_BF16))
+            return NMF_E_DTYPE;
+    } else {
+        m = V->d.rows;
+        n = V->d.cols;
+        if (!V->d.data || V->d.ld < n)
+            return NMF_E_ARG;
+        if (V->d.dt != NMF_F32)
+            return NMF_E_DTYPE;
+        if (Vt) {
+            if (Vt->is_sparse || Vt->d.rows != n || Vt->d.cols != m || Vt->d.ld < m || !Vt->d.data)
+                return NMF_E_SHAPE;
+            if (Vt->d.dt != NMF_F32)
+                return NMF_E_DTYPE;
+        }
+    }
+    if (m <= 0 || n <= 0)
+        return NMF_E_SHAPE;
+    CK(cudaSetDevice(h->device));
+
+    // ---- workspace layout
+    L.gS_w = gram_splits(m);
+    L.gS_h = gram_splits(n);
+    const int gS = L.gS_w > L.gS_h ? L.gS_w : L.gS_h;
+    int sw = 1, sh = 1;
+    SpmmPlan pw{}, ph{};
+    if (sparse) {
+        pw = spmm_plan(m, V->s.nnz);
+        ph = spmm_plan(n, Vt->s.nnz);
+    } else {
+        sw = cross_splits(m, n);
+        sh = cross_splits(n, m);
+    }
+    const bool need_vt = !sparse && !Vt;
+    if (o.objective < 0 || o.objective > 1 || (o.objective == 1 && sparse))
+        return NMF_E_NOTIMPL;
+    L.direct_obj = o.objective == 1;
+    const size_t n_objp = L.direct_obj ? objective_direct_partials(m, n) : 0;
+    Sizer z;
+    z.add<double>(n_objp);
+    z.add<float>((size_t)gS * r * r);
+    z.add<float>((size_t)r * r);
+    z.add<float>((size_t)r * r);
+    z.add<float>((size_t)r * r);
+    z.add<float>(r);
+    z.add<float>((size_t)r * r);
+    z.add<float>((size_t)r * r);
+    z.add<float>((size_t)sw * m * r);
+    z.add<float>((size_t)sh * n * r);
+    size_t spb = sparse ? std::max(spmm_workspace_bytes(pw, r), spmm_workspace_bytes(ph, r)) : 0;
+    z.add<char>(spb);
+    if (need_vt)
+        z.add<float>((size_t)m * n);
+    nmf_status st = ensure_ws(h, z.off);
+    if (st)
+        return st;
+    Arena a(h->ws, h->ws_cap);
+    L.obj_partials = a.take<double>(n_objp);
+    if (!sparse) {
+        L.V = (const float *)V->d.data;
+        L.ldv = V->d.ld;
+    }
+    L.Pg = a.take<float>((size_t)gS * r * r);
+    L.Gw = a.take<float>((size_t)r * r);
+    L.Gh = a.take<float>((size_t)r * r);
+    L.Qt = a.take<float>((size_t)r * r);
+    L.d = a.take<float>(r);
+    float *Qw = a.take<float>((size_t)r * r);
+    float *Qh = a.take<float>((size_t)r * r);
+    float *Cw = a.take<float>((size_t)sw * m * r);
+    float *Ch = a.take<float>((size_t)sh * n * r);
+    L.spws = a.take<char>(spb);
+    const float *vt_data = nullptr;
+    int64_t vt_ld = m;
+    if (need_vt) {
+        float *vtb = a.take<float>((size_t)m * n);
+        CK(launch_transpose_f32((const float *)V->d.data, m, n, V->d.ld, vtb, h->stream));
+        vt_data = vtb;
+    } else if (!sparse) {
+        vt_data = (const float *)Vt->d.data;
+        vt_ld = Vt->d.ld;
+    }
+
+    // half-step descriptions
+    HalfStep &hw = L.hw, &hh = L.hh;
+    hw = HalfStep{};
+    hh = HalfStep{};
+    hw.sparse = hh.sparse = sparse;
+    hw.rows = m;
+    hw.X = W;
+    hw.Xo = Ht;
+    hw.Ko = n;
+    hw.alpha = o.alpha_w;
+    hw.beta = o.beta_w;
+    hw.Cs = Cw;
+    hw.Q = Qw;
+    hh.rows = n;
+    hh.X = Ht;
+    hh.Xo = W;
+    hh.Ko = m;
+    hh.alpha = o.alpha_h;
+    hh.beta = o.beta_h;
+    hh.Cs = Ch;
+    hh.Q = Qh;
+    if (sparse) {
+        hw.csr = &V->s;
+        hw.plan = pw;
+        hw.nsplit = 1;
+        hh.csr = &Vt->s;
+        hh.plan = ph;
+        hh.nsplit = 1;
+    } else {
+        hw.A = (const float *)V->d.data;
+        hw.lda = V->d.ld;
+        hw.K = n;
+        hw.nsplit = sw;
+        hh.A = vt_data;
+        hh.lda = vt_ld;
+        hh.K = m;
+        hh.nsplit = sh;
+    }
+
+    cudaStream_t s = h->stream;
+    // ||V||^2 (constant of the trace identity), FP64
+    double *vv_dev = h->scal + 1;
+    if (sparse)
+        CK(launch_sumsq(V->s.vals, V->s.dt, V->s.nnz, vv_dev, h->partials, h->tickets + 1, s));
+    else if (V->d.ld == n)
+        CK(launch_sumsq(V->d.data, NMF_F32, m * n, vv_dev, h->partials, h->tickets + 1, s));
+    else
+        return NMF_E_NOTIMPL;   // strided dense V: pass a contiguous V
+    CK(cudaMemsetAsync(h->ctr, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(h->idev, 0, 2 * sizeof(int), s));
+    CK(cudaMemcpyAsync(&L.vv, vv_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+    // G_H = Ht^T Ht for the first W-update
+    st = gram_into(h, Ht, n, r, r, o.prec, L.Pg, L.gS_h, L.Gh);
+    if (st)
+        return st;
+
+    const bool gap_on = o.rel_gap_target > 0.0 && o.f_star > 0.0;
+    const int check = o.check_every > 0 ? o.check_every : 1;
+    std::vector<double> hist;
+    int done_iters = 0;
+    double Jlast = NAN;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    long long per_iter_launches = 0;
+    CK(prepare_nnls(r));
+    if (o.use_graph && o.outer_iters > 0) {
+        if (!h->cap)
+            CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+        CK(cudaStreamSynchronize(s));
+        long long before = nmf_launch_count();
+        prof_suspend(true);
+        h->stream = h->cap;
+        cudaError_t ce = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) {
+            h->stream = s;
+            prof_suspend(false);
+            return cuda_st(ce);
+        }
+        st = enqueue_iteration(h, L, o);
+        cudaGraph_t g2 = nullptr;
+        ce = cudaStreamEndCapture(h->cap, &g2);
+        h->stream = s;
+        prof_suspend(false);
+        if (st)
+            return st;
+        CK(ce);
+        graph = g2;
+        CK(cudaGraphInstantiate(&gexec, graph, 0));
+        per_iter_launches = nmf_launch_count() - before;
+        g_launches.fetch_sub(per_iter_launches);
+    }
+    bool have_j = false;
+    for (int t = 0; t < o.outer_iters; ++t) {
+        if (gexec) {
+            CK(cudaGraphLaunch(gexec, s));
+            count_launch((int)per_iter_launches);
+        } else {
+            st = enqueue_iteration(h, L, o);
+            if (st)
+                return st;
+        }
+        ++done_iters;
+        const bool last = t + 1 == o.outer_iters;
+        const bool check_now = gap_on && (((t + 1) % check == 0) || last);
+        if (o.obj_hist || check_now || (last && rep)) {
+            if ((st = enqueue_objective(h, L, o, o.f_star, o.rel_gap_target)))
+                return st;
+            have_j = true;
+        }
+        if (o.obj_hist || check_now) {
+            double J;
+            CK(cudaMemcpyAsync(&J, h->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (o.obj_hist)
+                o.obj_hist[t] = J;
+            Jlast = J;
+            if (gap_on && (J - o.f_star) / o.f_star <= o.rel_gap_target)
+                break;
+        }
+    }
+    if (!have_j && rep && done_iters > 0) {
+        if ((st = enqueue_objective(h, L, o, o.f_star, o.rel_gap_target)))
+            return st;
+    }
+    CK(cudaEventRecord(e1, s));
+    if (gexec) {
+        cudaGraphExecDestroy(gexec);
+        cudaGraphDestroy(graph);
+    }
+
+    // report: J, kbar, KKT of the last half-steps' NQPs
+    double *kk = h->scal + 4;
+    unsigned long long inner = 0;
+    if (rep) {
+        CK(cudaMemcpyAsync(&Jlast, h->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&inner, h->ctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        // KKT of the H-update just solved (its Q and C are still in place)
+        if (hh.nsplit > 1)
+            CK(launch_sum_slices(hh.Cs, hh.nsplit, n * r, hh.Cs, s));
+        CK(launch_kkt(hh.Q, hh.Cs, n, r, hh.alpha, Ht, kk, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rep) {
+        double kkv[2];
+        CK(cudaMemcpy(kkv, kk, sizeof(kkv), cudaMemcpyDeviceToHost));
+        rep->iters_done = done_iters;
+        rep->objective = Jlast;
+        rep->rel_gap = o.f_star > 0.0 ? (Jlast - o.f_star) / o.f_star : 0.0;
+        rep->inner_total = (int64_t)inner;
+        rep->kbar = done_iters > 0 ? (double)inner / ((double)done_iters * (double)(m + n)) : 0.0;
+        rep->kkt_max = kkv[0];
+        rep->ms_total = ms;
+    }
+    return nmf_sync(h);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// projection onto a fixed basis
+// ---------------------------------------------------------------------------
+NMF_API nmf_status nmf_project(nmf_handle h, const float *Qt, const float *d, const float *W,
+                               int64_t wrows, int r, const nmf_csr *VnewT, float *Hnew,
+                               const nmf_nnls_opts *opts)
+{
+    if (!h || !Qt || !d || !W || !VnewT || !Hnew)
+        return NMF_E_ARG;
+    if (bad_r(r) || wrows < 0 || VnewT->rows < 0 || VnewT->cols != wrows)
+        return NMF_E_SHAPE;
+    if (!VnewT->rowptr || (VnewT->nnz > 0 && (!VnewT->colidx || !VnewT->vals)))
+        return NMF_E_ARG;
+    if (VnewT->dt != NMF_F32 && VnewT->dt != NMF_BF16)
+        return NMF_E_DTYPE;
+    const int64_t w = VnewT->rows;
+    if (w == 0)
+        return NMF_OK;
+    nmf_status st = ensure_ws(h, sizeof(float) * (size_t)w * r + 256);
+    if (st)
+        return st;
+    float *C = reinterpret_cast<float *>(h->ws);
+    CK(launch_spmm_rowwarp(VnewT->rowptr, VnewT->colidx, VnewT->vals, VnewT->dt, w, W, r, C,
+                           h->stream));
+    return nmf_nnls_update(h, Qt, d, C, w, r, 0.f, Hnew, opts, nullptr);
+}

@@ -1,0 +1,417 @@
+// Small kernels around the products:
+//  * rescale   - anti-lopsided rescaling of the shared Gram (§3.4 Eq. 3)
+//  * objective - J by the trace identity, FP64 (Def. 1; Table 4 reports
+//                1/2||V - WH||^2), with the L1/L2 terms of §3.5
+//  * kkt       - optimality residuals of Eq. 2, FP64
+//  * sumsq     - ||V||_F^2 in FP64 (constant term of the trace identity)
+// All reductions are two-level with a fixed grid and a last-block finish, so
+// their results do not depend on scheduling.
+#include "nmf_internal.cuh"
+
+namespace nmfi {
+namespace {
+
+constexpr int kRedBlocks = 256;
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-wide FP64 sum, fixed order (warp tree, then warp 0 over warp sums)
+__device__ double block_sum_d(double v, double *sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0)
+        sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < nw ? sh[lane] : 0.0;
+        t = warp_sum_d(t);
+    }
+    return t;   // valid in thread 0
+}
+
+__global__ void k_rescale(const float *__restrict__ P, int nsplit, int r, float beta,
+                          float *__restrict__ G, float *__restrict__ Q, float *__restrict__ Qt,
+                          float *__restrict__ dout)
+{
+    __shared__ float sd[kMaxRank];
+    const int n = r * r;
+    // diagonal first: d_i = sqrt(Q_ii), 0 marks a dead coordinate
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < nsplit; ++k)
+            s += P[(int64_t)k * n + i * r + i];
+        const float qii = s + beta;
+        sd[i] = qii > 0.f ? sqrtf(qii) : 0.f;
+        if (dout)
+            dout[i] = qii > 0.f ? sd[i] : 1.f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < nsplit; ++k)
+            s += P[(int64_t)k * n + e];
+        const int i = e / r, j = e - i * r;
+        if (G)
+            G[e] = s;
+        const float q = i == j ? s + beta : s;
+        if (Q)
+            Q[e] = q;
+        if (Qt) {
+            float v;
+            if (sd[i] == 0.f || sd[j] == 0.f)
+                v = 0.f;
+            else if (i == j)
+                v = 1.f;
+            else
+                v = q / (sd[i] * sd[j]);
+            Qt[e] = v;
+        }
+    }
+}
+
+// J = 1/2 (vv - 2<Ht, Ch> + <Gw, Gh>) + aw sum W + ah sum Ht + bw/2 tr Gw + bh/2 tr Gh
+__global__ void __launch_bounds__(kRedThreads) k_objective(const ObjArgs a)
+{
+    __shared__ double sh[32];
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nh = a.n * a.r, nw = a.m * a.r;
+    double dot = 0.0, sw = 0.0, shh = 0.0;
+    for (int64_t e = tid; e < nh; e += stride) {
+        float c = 0.f;
+        for (int s = 0; s < a.nsplit; ++s)
+            c += a.Ch[s * a.ch_stride + e];
+        const double h = (double)a.Ht[e];
+        dot += h * (double)c;
+        shh += h;
+    }
+    for (int64_t e = tid; e < nw; e += stride)
+        sw += (double)a.W[e];
+    double v0 = block_sum_d(dot, sh);
+    double v1 = block_sum_d(sw, sh);
+    double v2 = block_sum_d(shh, sh);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        a.partials[blockIdx.x * 3 + 0] = v0;
+        a.partials[blockIdx.x * 3 + 1] = v1;
+        a.partials[blockIdx.x * 3 + 2] = v2;
+        __threadfence();
+        unsigned t = atomicAdd(a.ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last)
+        return;
+    __threadfence();
+    // last block: partial sums in block order, then the r x r terms
+    double gg = 0.0, trw = 0.0, trh = 0.0;
+    const int rr = a.r * a.r;
+    for (int e = threadIdx.x; e < rr; e += blockDim.x) {
+        gg += (double)a.Gw[e] * (double)a.Gh[e];
+        if (e / a.r == e % a.r) {
+            trw += (double)a.Gw[e];
+            trh += (double)a.Gh[e];
+        }
+    }
+    gg = block_sum_d(gg, sh);
+    trw = block_sum_d(trw, sh);
+    trh = block_sum_d(trh, sh);
+    if (threadIdx.x == 0) {
+        volatile double *pp = a.partials;
+        double d = 0.0, s1 = 0.0, s2 = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            d += pp[b * 3 + 0];
+            s1 += pp[b * 3 + 1];
+            s2 += pp[b * 3 + 2];
+        }
+        double J = 0.5 * (a.vv - 2.0 * d + gg) + (double)a.aw * s1 + (double)a.ah * s2 +
+                   0.5 * (double)a.bw * trw + 0.5 * (double)a.bh * trh;
+        *a.J = J;
+        if (a.hist && a.t)
+            a.hist[*a.t] = J;
+        if (a.done_flag && a.f_star > 0.0 && (J - a.f_star) / a.f_star <= a.gap_target)
+            *a.done_flag = 1;
+        *a.ticket = 0u;   // ready for the next launch
+    }
+}
+
+// KKT residuals of one factor, FP64.  One warp per row; Q and the row in smem.
+__global__ void __launch_bounds__(256) k_kkt(const float *__restrict__ Q,
+                                             const float *__restrict__ C, int64_t rows, int r,
+                                             float alpha, const float *__restrict__ X,
+                                             unsigned long long *out)
+{
+    __shared__ float sx[8][kMaxRank];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double m1 = 0.0, m2 = 0.0;
+    for (int64_t row = (int64_t)blockIdx.x * 8 + w; row < rows; row += (int64_t)gridDim.x * 8) {
+        for (int c = lane; c < r; c += 32)
+            sx[w][c] = X[row * r + c];
+        __syncwarp();
+        for (int j = lane; j < r; j += 32) {
+            double gj = (double)alpha - (double)C[row * r + j];
+            for (int k = 0; k < r; ++k)
+                gj += (double)__ldg(Q + j * r + k) * (double)sx[w][k];
+            const double x = (double)sx[w][j];
+            const double a1 = fabs(x < gj ? x : gj), a2 = fabs(x * gj);
+            m1 = a1 > m1 ? a1 : m1;
+            m2 = a2 > m2 ? a2 : m2;
+        }
+        __syncwarp();
+    }
+    // non-negative doubles order like their bit patterns
+    for (int o = 16; o > 0; o >>= 1) {
+        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    if (lane == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(m1));
+        atomicMax(out + 1, (unsigned long long)__double_as_longlong(m2));
+    }
+}
+
+// J = 1/2 sum_ij (V_ij - W_i . Ht_j)^2 + penalties, the residual formed
+// element by element: W_i . Ht_j by an FP32 fma chain over r, the square
+// accumulated in FP64.  Avoids the cancellation of the trace identity.  CTA
+// tile 64 x 64 of V, k-chunks of 32 of the factors staged in shared memory;
+// thread (ty, tx) owns rows ty + 16 i and columns tx + 16 j (i, j < 4).
+__global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
+{
+    constexpr int BT = 64, KC = 32;
+    __shared__ float Ws[KC][BT + 1];
+    __shared__ float Hs[KC][BT + 1];
+    __shared__ double sh[32];
+    __shared__ bool last;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int64_t tiles_n = (a.n + BT - 1) / BT;
+    const int64_t i0 = (blockIdx.x / tiles_n) * BT, j0 = (blockIdx.x % tiles_n) * BT;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < a.r; k0 += KC) {
+        for (int idx = tid; idx < BT * KC; idx += 256) {
+            int rr = idx / KC, kk = idx - rr * KC;
+            int64_t gi = i0 + rr, gj = j0 + rr;
+            int gk = k0 + kk;
+            Ws[kk][rr] = (gi < a.m && gk < a.r) ? a.W[gi * a.r + gk] : 0.f;
+            Hs[kk][rr] = (gj < a.n && gk < a.r) ? a.Ht[gj * a.r + gk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < KC; ++kk) {
+            float w[4], hh[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                w[i] = Ws[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                hh[j] = Hs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    acc[i][j] = fmaf(w[i], hh[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    double fit = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t gi = i0 + ty + 16 * i;
+        if (gi >= a.m)
+            continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t gj = j0 + tx + 16 * j;
+            if (gj < a.n) {
+                double e = (double)(a.V[gi * a.ldv + gj] - acc[i][j]);
+                fit += e * e;
+            }
+        }
+    }
+    // penalty sums, grid-strided over the (small) factors
+    double sw = 0.0, sw2 = 0.0, shh = 0.0, sh2 = 0.0;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + tid, gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = gt; e < a.m * a.r; e += gs) {
+        double v = a.W[e];
+        sw += v;
+        sw2 += v * v;
+    }
+    for (int64_t e = gt; e < a.n * a.r; e += gs) {
+        double v = a.Ht[e];
+        shh += v;
+        sh2 += v * v;
+    }
+    double v[5] = {fit, sw, sw2, shh, sh2};
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        v[q] = block_sum_d(v[q], sh);
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            a.partials[(int64_t)blockIdx.x * 5 + q] = v[q];
+        __threadfence();
+        last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last)
+        return;
+    __threadfence();
+    // last block: thread t sums blocks t, t + 256, ... (fixed order), then
+    // the block tree - the same grouping on every run
+    volatile double *pp = a.partials;
+    double t[5] = {0, 0, 0, 0, 0};
+    for (unsigned b = tid; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            t[q] += pp[(int64_t)b * 5 + q];
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        t[q] = block_sum_d(t[q], sh);
+    if (tid == 0) {
+        *a.J = 0.5 * t[0] + (double)a.aw * t[1] + 0.5 * (double)a.bw * t[2] +
+               (double)a.ah * t[3] + 0.5 * (double)a.bh * t[4];
+        *a.ticket = 0u;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ double as_d(T v);
+template <>
+__device__ __forceinline__ double as_d<float>(float v) { return (double)v; }
+template <>
+__device__ __forceinline__ double as_d<__nv_bfloat16>(__nv_bfloat16 v)
+{
+    return (double)__bfloat162float(v);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_sumsq(const T *__restrict__ x, int64_t n,
+                                                       double *out, double *partials,
+                                                       unsigned *ticket)
+{
+    __shared__ double sh[32];
+    __shared__ bool last;
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double v = as_d<T>(x[e]);
+        s += v * v;
+    }
+    s = block_sum_d(s, sh);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = s;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        volatile double *pp = partials;
+        double t = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b)
+            t += pp[b];
+        *out = t;
+        *ticket = 0u;
+    }
+}
+
+__global__ void k_f32_to_bf16(const float *__restrict__ x, int64_t n, __nv_bfloat16 *__restrict__ y)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = __float2bfloat16_rn(x[e]);
+}
+
+}  // namespace
+
+cudaError_t launch_rescale(const float *P, int nsplit, int r, float beta, float *G, float *Q,
+                           float *Qt, float *d, cudaStream_t s)
+{
+    ProfScope prof_(KC_RESCALE, s);
+    k_rescale<<<1, 1024, 0, s>>>(P, nsplit, r, beta, G, Q, Qt, d);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective(const ObjArgs &a, cudaStream_t s)
+{
+    ProfScope prof_(KC_OBJECTIVE, s);
+    k_objective<<<kRedBlocks, kRedThreads, 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+size_t objective_direct_partials(int64_t m, int64_t n)
+{
+    return (size_t)((m + 63) / 64) * (size_t)((n + 63) / 64) * 5;
+}
+
+cudaError_t launch_objective_direct(const ObjDirectArgs &a, cudaStream_t s)
+{
+    ProfScope prof_(KC_OBJECTIVE, s);
+    const int64_t tiles = ((a.m + 63) / 64) * ((a.n + 63) / 64);
+    if (tiles <= 0 || tiles > 0x7fffffff)
+        return cudaErrorInvalidValue;
+    k_objective_direct<<<(unsigned)tiles, 256, 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kkt(const float *Q, const float *C, int64_t rows, int r, float alpha,
+                       const float *X, double *out, cudaStream_t s)
+{
+    ProfScope prof_(KC_OTHER, s);
+    cudaMemsetAsync(out, 0, 2 * sizeof(double), s);
+    if (rows <= 0)
+        return cudaGetLastError();
+    int64_t blocks = (rows + 7) / 8;
+    if (blocks > 1024)
+        blocks = 1024;
+    k_kkt<<<(unsigned)blocks, 256, 0, s>>>(Q, C, rows, r, alpha, X,
+                                           reinterpret_cast<unsigned long long *>(out));
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(const void *x, nmf_dtype dt, int64_t n, double *out, double *partials,
+                         unsigned *ticket, cudaStream_t s)
+{
+    ProfScope prof_(KC_OTHER, s);
+    if (dt == NMF_BF16)
+        k_sumsq<__nv_bfloat16><<<kRedBlocks, kRedThreads, 0, s>>>(
+            reinterpret_cast<const __nv_bfloat16 *>(x), n, out, partials, ticket);
+    else
+        k_sumsq<float><<<kRedBlocks, kRedThreads, 0, s>>>(reinterpret_cast<const float *>(x), n,
+                                                          out, partials, ticket);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_bf16(const float *x, int64_t n, __nv_bfloat16 *y, cudaStream_t s)
+{
+    ProfScope prof_(KC_OTHER, s);
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 8192)
+        blocks = 8192;
+    if (blocks < 1)
+        return cudaSuccess;
+    k_f32_to_bf16<<<(unsigned)blocks, 256, 0, s>>>(x, n, y);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace nmfi

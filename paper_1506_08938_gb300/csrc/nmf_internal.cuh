@@ -1,0 +1,131 @@
+// Internal declarations shared by the translation units of libnmf.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/nmf.h"
+
+#define NMF_API extern "C" __attribute__((visibility("default")))
+
+namespace nmfi {
+
+constexpr int kMaxRank = 128;
+
+// Device status word bits (latched until nmf_sync).
+constexpr unsigned kStNonFinite = 1u;
+constexpr unsigned kStTimeout = 2u;
+
+void count_launch(int n = 1);
+
+// Per-kernel-class device time (CUDA events around launches while enabled).
+enum KClass { KC_GRAM = 0, KC_CROSS, KC_SPMM, KC_RESCALE, KC_NNLS, KC_OBJECTIVE, KC_OTHER,
+              KC_COUNT };
+void prof_mark(int cls, cudaStream_t s, bool begin);
+struct ProfScope {
+    int cls;
+    cudaStream_t s;
+    ProfScope(int c, cudaStream_t st) : cls(c), s(st) { prof_mark(cls, s, true); }
+    ~ProfScope() { prof_mark(cls, s, false); }
+};
+void prof_suspend(bool on);   // no events while a stream is being captured
+
+// ---- NNLS (Alg. 3) --------------------------------------------------------
+struct NnlsArgs {
+    const float *Qt;        // r x r rescaled Gram (row-major, symmetric)
+    const float *d;         // r
+    const float *C;         // nsplit slices of rows x r, slice stride c_stride
+    int nsplit;
+    int64_t c_stride;
+    int64_t rows;
+    int r;
+    float alpha;
+    float *X;               // rows x r, in: warm start, out: solution
+    int max_inner;
+    float eps;
+    int cd_steps;           // < 0: r
+    int maxstop_mode;
+    float maxstop;          // threshold for mode 1
+    int32_t *iters;         // optional per-row counts
+    unsigned long long *iter_total;   // optional sum of counts
+    unsigned *s_final_max;  // optional: atomicMax of final ||f||^2 bits
+    unsigned *status;       // optional device status word
+};
+cudaError_t launch_nnls(const NnlsArgs &a, cudaStream_t s);
+cudaError_t prepare_nnls(int r);
+
+// ---- Gram / cross term (SIMT FP32) ----------------------------------------
+// partial Gram slices: P[s] = X[k0:k1]^T X[k0:k1], s < nsplit, each r x r.
+cudaError_t launch_gram_partial(const float *X, int64_t rows, int64_t ld, int r, float *P,
+                                int nsplit, cudaStream_t s);
+int gram_splits(int64_t rows);
+// partial cross slices: P[s] = A[:, k0:k1] B[k0:k1, :], each M x r.
+cudaError_t launch_cross_dense_f32(const float *A, int64_t M, int64_t K, int64_t lda,
+                                   const float *B, int r, float *P, int nsplit,
+                                   cudaStream_t s);
+int cross_splits(int64_t M, int64_t K);
+// C = sum of nsplit slices (each n elements)
+cudaError_t launch_sum_slices(const float *P, int nsplit, int64_t n, float *out, cudaStream_t s);
+// out = A^T (A rows x cols, lda) -> cols x rows
+cudaError_t launch_transpose_f32(const float *A, int64_t rows, int64_t cols, int64_t lda,
+                                 float *out, cudaStream_t s);
+
+// ---- sparse cross term ----------------------------------------------------
+struct SpmmPlan {
+    int64_t pieces = 0;     // number of merge-path pieces
+    int items_per_piece = 0;
+};
+SpmmPlan spmm_plan(int64_t rows, int64_t nnz);
+size_t spmm_workspace_bytes(const SpmmPlan &p, int r);
+cudaError_t launch_spmm_csr(const int64_t *rowptr, const int32_t *colidx, const void *vals,
+                            nmf_dtype vdt, int64_t rows, int64_t nnz, const float *B, int r,
+                            float *C, const SpmmPlan &plan, void *ws, cudaStream_t s);
+// row-per-warp variant: deterministic per row regardless of batch composition
+cudaError_t launch_spmm_rowwarp(const int64_t *rowptr, const int32_t *colidx, const void *vals,
+                                nmf_dtype vdt, int64_t rows, const float *B, int r, float *C,
+                                cudaStream_t s);
+
+// ---- rescale / reductions -------------------------------------------------
+// G = sum of nsplit Gram slices; Q = G + beta I; d, Qt (rescaled).  Any output
+// pointer may be NULL.
+cudaError_t launch_rescale(const float *P, int nsplit, int r, float beta, float *G, float *Q,
+                           float *Qt, float *d, cudaStream_t s);
+// FP64 trace-identity objective (see nmf_objective)
+struct ObjArgs {
+    double vv;
+    const float *W; int64_t m;
+    const float *Ht; int64_t n;
+    int r;
+    const float *Ch; int nsplit; int64_t ch_stride;
+    const float *Gw; const float *Gh;
+    float aw, ah, bw, bh;
+    double *J;              // device scalar out
+    double *hist;           // optional device array, hist[*t] = J
+    const int *t;           // device iteration counter (with hist)
+    double f_star, gap_target;
+    int *done_flag;         // optional: set to 1 when gap <= target
+    double *partials;       // workspace: grid doubles x 3
+    unsigned *ticket;       // workspace counter (zeroed)
+};
+cudaError_t launch_objective(const ObjArgs &a, cudaStream_t s);
+// FP64 objective from the element-wise residual (dense V)
+struct ObjDirectArgs {
+    const float *V; int64_t ldv;
+    const float *W; int64_t m;
+    const float *Ht; int64_t n;
+    int r;
+    float aw, ah, bw, bh;
+    double *J;
+    double *partials;       // objective_direct_partials(m, n) doubles
+    unsigned *ticket;
+};
+size_t objective_direct_partials(int64_t m, int64_t n);
+cudaError_t launch_objective_direct(const ObjDirectArgs &a, cudaStream_t s);
+cudaError_t launch_kkt(const float *Q, const float *C, int64_t rows, int r, float alpha,
+                       const float *X, double *out, cudaStream_t s);
+cudaError_t launch_sumsq(const void *x, nmf_dtype dt, int64_t n, double *out, double *partials,
+                         unsigned *ticket, cudaStream_t s);
+cudaError_t launch_f32_to_bf16(const float *x, int64_t n, __nv_bfloat16 *y, cudaStream_t s);
+
+}  // namespace nmfi
