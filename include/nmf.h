@@ -232,6 +232,31 @@ nmf_status nmf_project(nmf_handle h, const float *Qt, const float *d, const floa
                        int64_t wrows, int r, const nmf_csr *VnewT, float *Hnew,
                        const nmf_nnls_opts *opts);
 
+/* ---- allocation-free variant ----------------------------------------------- */
+
+/* nmf_gram without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc - code running
+ * under an allocator that must own every device byte (a framework's caching
+ * allocator or a fixed memory budget reserved up front), real-time or
+ * plugin code that may not take the driver's allocation path, and callers
+ * that cannot create an nmf_handle (whose workspace is allocated).
+ *
+ * Computes Q = X^T X + beta I exactly like nmf_gram with NMF_PREC_FP32
+ * (X rows x r F32 device memory, ld >= r; Q r x r F32 device memory),
+ * enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
+ * Its split-K partial sums use one fixed device array inside the library
+ * (about 4.2 MB, room for 63 partial r x r slices at r <= 128), which every
+ * GPU that loads the library holds until the process exits.
+ *
+ * Limits and errors: r > 128 returns NMF_E_SHAPE (the array holds r <= 128);
+ * NULL pointers NMF_E_ARG; non-F32 X NMF_E_DTYPE; a failed CUDA call
+ * NMF_E_CUDA.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the one array: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller. */
+nmf_status nmf_gram_noalloc(const nmf_dense *X, float beta, float *Q, void *cuda_stream);
+
 /* ---- instrumentation ------------------------------------------------------- */
 
 /* Kernel classes for nmf_profile_read. */

@@ -98,6 +98,7 @@ def _load():
                             C.POINTER(SolveOpts), C.POINTER(Report)]
     L.nmf_project.argtypes = [_P, _P, _P, _P, C.c_int64, C.c_int, C.POINTER(Csr), _P,
                               C.POINTER(NnlsOpts)]
+    L.nmf_gram_noalloc.argtypes = [C.POINTER(Dense), C.c_float, _P, _P]
     L.nmf_profile_enable.argtypes = [C.c_int]
     L.nmf_profile_read.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     return L
@@ -251,6 +252,20 @@ def nmf_gram(h: Handle, X, beta=0.0, prec="fp32", Q=None):
     Q = Q if Q is not None else torch.empty(r, r, device=X.device, dtype=torch.float32)
     d = dense(X)
     _check(lib().nmf_gram(h.h, C.byref(d), float(beta), PREC[prec], _ptr(Q)), "nmf_gram")
+    return Q
+
+
+def nmf_gram_noalloc(X, beta=0.0, Q=None, stream=None):
+    """Gram without any allocation inside the library (no handle needed); Q
+    must be preallocated by the caller when it cannot allocate either."""
+    import torch
+    _need_cuda(X)
+    r = X.shape[1]
+    Q = Q if Q is not None else torch.empty(r, r, device=X.device, dtype=torch.float32)
+    stream = stream if stream is not None else torch.cuda.current_stream(X.device)
+    d = dense(X)
+    _check(lib().nmf_gram_noalloc(C.byref(d), float(beta), _ptr(Q),
+                                  C.c_void_p(stream.cuda_stream)), "nmf_gram_noalloc")
     return Q
 
 
