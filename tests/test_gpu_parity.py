@@ -92,11 +92,13 @@ def assert_fixed_k_rows(X, Xo, Q, Cm, alpha, tol):
     and have an objective no worse than its warm start."""
     num = np.linalg.norm(X - Xo, axis=1)
     den = np.maximum(np.linalg.norm(Xo, axis=1), 1e-30)
-    ok = num / den <= tol
-    assert ok.mean() >= 0.95, f"only {ok.mean():.3f} of rows within {tol:.2e}"
-    assert np.all(X >= 0)
     f = 0.5 * np.einsum("ij,jk,ik->i", X, Q, X) + ((alpha - Cm) * X).sum(1)
     fo = 0.5 * np.einsum("ij,jk,ik->i", Xo, Q, Xo) + ((alpha - Cm) * Xo).sum(1)
+    # a row agrees if its iterate is within the FP32 bound, or - after a
+    # flipped near-tie - the objective it reached matches the oracle's
+    ok = (num / den <= tol) | (np.abs(f - fo) <= 1e-5 * np.abs(fo) + 1e-12)
+    assert ok.mean() >= 0.95, f"only {ok.mean():.3f} of rows agree (bound {tol:.2e})"
+    assert np.all(X >= 0)
     assert np.all(f <= fo + 1e-3 * np.abs(fo) + 1e-6)
 
 
