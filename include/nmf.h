@@ -54,15 +54,24 @@ typedef enum {
 
 typedef enum { NMF_F32 = 0, NMF_BF16 = 1, NMF_F64 = 2 } nmf_dtype;
 
-/* Arithmetic of the Gram and cross-term products (the NNLS sweeps are always
- * FP32).  FP32: products and sums in FP32.  TF32 / BF16: operands rounded to
- * that type, FP32 accumulation.  BF16X2: each operand split into a BF16 high
- * part and a BF16 low part, three products summed in FP32. */
+/* Arithmetic of the dense cross-term products (the NNLS sweeps are always
+ * FP32, the Gram matrices FP32 on CUDA cores).
+ *  FP32       FP32-accurate: on tcgen05 tensor cores each operand is split
+ *             into a TF32-exact high part and its remainder and
+ *             hi*hi + hi*lo + lo*hi is accumulated in FP32 (relative error
+ *             ~1e-6 like FP32); falls back to FP32_SIMT when the data's row
+ *             pitch is not a multiple of 16 bytes.
+ *  TF32       operands truncated to TF32 (10-bit mantissa), FP32 accumulate.
+ *  BF16       operands rounded to BF16, FP32 accumulate (the solve keeps a
+ *             BF16 copy of V and V^T on the device).
+ *  BF16X2     reserved (split BF16); not implemented.
+ *  FP32_SIMT  plain FP32 fused multiply-adds on CUDA cores. */
 typedef enum {
     NMF_PREC_FP32 = 0,
     NMF_PREC_TF32 = 1,
     NMF_PREC_BF16 = 2,
-    NMF_PREC_BF16X2 = 3
+    NMF_PREC_BF16X2 = 3,
+    NMF_PREC_FP32_SIMT = 4
 } nmf_prec;
 
 typedef struct nmf_ctx *nmf_handle;

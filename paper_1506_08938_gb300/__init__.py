@@ -22,7 +22,7 @@ NMF_OK, NMF_E_ARG, NMF_E_SHAPE, NMF_E_DTYPE, NMF_E_NOMEM, NMF_E_CUDA = 0, 1, 2, 
 NMF_E_NONFINITE, NMF_E_TIMEOUT, NMF_E_BUSY, NMF_E_NOTIMPL = 6, 7, 8, 9
 # dtypes / precisions
 NMF_F32, NMF_BF16, NMF_F64 = 0, 1, 2
-PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x2": 3}
+PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x2": 3, "fp32_simt": 4}
 
 
 class NmfError(RuntimeError):

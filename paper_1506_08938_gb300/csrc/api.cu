@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "nmf_internal.cuh"
@@ -382,8 +383,8 @@ NMF_API nmf_status nmf_gram(nmf_handle h, const nmf_dense *X, float beta, nmf_pr
         return NMF_E_SHAPE;
     if (X->dt != NMF_F32)
         return NMF_E_DTYPE;
-    if (prec != NMF_PREC_FP32)
-        return NMF_E_NOTIMPL;
+    if (prec < NMF_PREC_FP32 || prec > NMF_PREC_FP32_SIMT)
+        return NMF_E_ARG;   // every precision computes the Gram in FP32
     const int r = (int)X->cols;
     const int S = gram_splits(X->rows);
     Sizer z;
@@ -426,10 +427,44 @@ NMF_API nmf_status nmf_cross(nmf_handle h, const nmf_matrix *V, const float *B, 
     const nmf_dense &d = V->d;
     if (d.rows < 0 || d.cols < 0 || d.ld < d.cols || (!d.data && d.rows > 0))
         return NMF_E_SHAPE;
-    if (d.dt != NMF_F32)
-        return NMF_E_DTYPE;
-    if (prec != NMF_PREC_FP32)
+    int mode = -1;
+    if (prec == NMF_PREC_BF16) {
+        if (d.dt != NMF_BF16)
+            return NMF_E_DTYPE;
+        if (!tc_supported(d.ld, TC_BF16, d.data))
+            return NMF_E_SHAPE;
+        mode = TC_BF16;
+    } else if (prec == NMF_PREC_TF32 || prec == NMF_PREC_FP32 || prec == NMF_PREC_FP32_SIMT) {
+        if (d.dt != NMF_F32)
+            return NMF_E_DTYPE;
+        const int want = prec == NMF_PREC_TF32 ? TC_TF32 : TC_TF32X3;
+        if (prec != NMF_PREC_FP32_SIMT && tc_supported(d.ld, want, d.data))
+            mode = want;
+        else if (prec == NMF_PREC_TF32)
+            return NMF_E_SHAPE;
+    } else {
         return NMF_E_NOTIMPL;
+    }
+    if (mode >= 0) {
+        if (d.rows == 0)
+            return NMF_OK;
+        const TcPlan pl = tc_plan(d.rows, d.cols, r, mode);
+        Sizer z;
+        z.add<char>(tc_pack_bytes(d.cols, r, mode));
+        z.add<float>((size_t)pl.nslices * d.rows * r);
+        nmf_status st = ensure_ws(h, z.off);
+        if (st)
+            return st;
+        Arena a(h->ws, h->ws_cap);
+        void *pack = a.take<char>(tc_pack_bytes(d.cols, r, mode));
+        float *P = pl.nslices == 1 ? C : a.take<float>((size_t)pl.nslices * d.rows * r);
+        CK(launch_tc_pack(B, d.cols, r, mode, pack, h->stream));
+        CK(launch_tc_cross(d.data, d.rows, d.cols, d.ld, r, mode, pack, P, pl, h->status,
+                           h->stream));
+        if (pl.nslices > 1)
+            CK(launch_sum_slices(P, pl.nslices, d.rows * r, C, h->stream));
+        return NMF_OK;
+    }
     const int S = cross_splits(d.rows, d.cols);
     if (S == 1) {
         CK(launch_cross_dense_f32((const float *)d.data, d.rows, d.cols, d.ld, B, r, C, 1,
@@ -574,7 +609,7 @@ struct HalfStep {
     const float *A;
     int64_t lda, K;
     const nmf_csr *csr;
-    SpmmPlan plan;
+    SpmmPlan spplan;
     int64_t rows;       // number of NQPs (rows of the factor updated)
     float *X;           // factor updated (rows x r)
     const float *Xo;    // other factor (K x r)
@@ -584,6 +619,11 @@ struct HalfStep {
     int nsplit;
     float *Q;           // Q = G_other + beta I (kept for KKT)
     unsigned *smax;     // maxStop bits for this factor
+    int tc_mode;        // -1: CUDA-core FP32 cross term
+    const void *Atc;    // tensor-core operand (F32, or the BF16 copy)
+    int64_t lda_tc;
+    TcPlan plan;        // stream-K plan of the tensor-core cross term
+    void *pack;         // packed other factor
 };
 
 struct Loop {
@@ -609,7 +649,11 @@ nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, const float *Gother)
     // cross term C = V X_other
     if (s.sparse) {
         CK(launch_spmm_csr(s.csr->rowptr, s.csr->colidx, s.csr->vals, s.csr->dt, s.csr->rows,
-                           s.csr->nnz, s.Xo, L.r, s.Cs, s.plan, L.spws, st));
+                           s.csr->nnz, s.Xo, L.r, s.Cs, s.spplan, L.spws, st));
+    } else if (s.tc_mode >= 0) {
+        CK(launch_tc_pack(s.Xo, s.K, L.r, s.tc_mode, s.pack, st));
+        CK(launch_tc_cross(s.Atc, s.rows, s.K, s.lda_tc, L.r, s.tc_mode, s.pack, s.Cs, s.plan,
+                           h->status, st));
     } else {
         CK(launch_cross_dense_f32(s.A, s.rows, s.K, s.lda, s.Xo, L.r, s.Cs, s.nsplit, st));
     }
@@ -827,7 +871,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     const nmf_solve_opts o = *opts;
     if (o.outer_iters < 0)
         return NMF_E_ARG;
-    if (o.prec != NMF_PREC_FP32)
+    if (o.prec < NMF_PREC_FP32 || o.prec > NMF_PREC_FP32_SIMT || o.prec == NMF_PREC_BF16X2)
         return NMF_E_NOTIMPL;
     Loop L{};
     L.r = r;
@@ -879,6 +923,31 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
         sh = cross_splits(n, m);
     }
     const bool need_vt = !sparse && !Vt;
+    // dense cross-term arithmetic: tensor cores when the layouts allow TMA
+    int mode = -1;
+    if (!sparse) {
+        const int64_t vt_ld_req = Vt ? Vt->d.ld : m;
+        if (o.prec == NMF_PREC_BF16) {
+            if (n % 8 || m % 8 || !tc_supported(n, TC_BF16, V->d.data))
+                return NMF_E_NOTIMPL;
+            mode = TC_BF16;
+        } else if (o.prec != NMF_PREC_FP32_SIMT) {
+            const int want = o.prec == NMF_PREC_TF32 ? TC_TF32 : TC_TF32X3;
+            if (tc_supported(V->d.ld, want, V->d.data) && vt_ld_req % 4 == 0 &&
+                (!Vt || tc_supported(Vt->d.ld, want, Vt->d.data)))
+                mode = want;
+            else if (o.prec == NMF_PREC_TF32)
+                return NMF_E_NOTIMPL;
+        }
+        if (mode >= 0) {
+            L.hw.plan = tc_plan(m, n, r, mode);
+            L.hh.plan = tc_plan(n, m, r, mode);
+            sw = L.hw.plan.nslices;
+            sh = L.hh.plan.nslices;
+        }
+    }
+    const size_t pack_b = mode >= 0 ? std::max(tc_pack_bytes(n, r, mode), tc_pack_bytes(m, r, mode)) : 0;
+    const size_t bf_b = mode == TC_BF16 ? sizeof(__nv_bfloat16) * (size_t)m * n : 0;
     if (o.objective < 0 || o.objective > 1 || (o.objective == 1 && sparse))
         return NMF_E_NOTIMPL;
     L.direct_obj = o.objective == 1;
@@ -898,6 +967,9 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     z.add<char>(spb);
     if (need_vt)
         z.add<float>((size_t)m * n);
+    z.add<char>(pack_b);
+    z.add<char>(bf_b);
+    z.add<char>(bf_b);
     nmf_status st = ensure_ws(h, z.off);
     if (st)
         return st;
@@ -927,11 +999,24 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
         vt_data = (const float *)Vt->d.data;
         vt_ld = Vt->d.ld;
     }
+    void *pack = a.take<char>(pack_b);
+    __nv_bfloat16 *vbf = a.take<__nv_bfloat16>(bf_b / 2);
+    __nv_bfloat16 *vtbf = a.take<__nv_bfloat16>(bf_b / 2);
+    if (mode == TC_BF16) {
+        // BF16 copies of V and V^T (contiguous), made once per solve
+        CK(launch_f32_to_bf16((const float *)V->d.data, m * n, vbf, h->stream));
+        if (vt_ld != m)
+            return NMF_E_NOTIMPL;
+        CK(launch_f32_to_bf16(vt_data, m * n, vtbf, h->stream));
+    }
 
     // half-step descriptions
     HalfStep &hw = L.hw, &hh = L.hh;
+    const TcPlan plan_w = hw.plan, plan_h = hh.plan;
     hw = HalfStep{};
     hh = HalfStep{};
+    hw.plan = plan_w;
+    hh.plan = plan_h;
     hw.sparse = hh.sparse = sparse;
     hw.rows = m;
     hw.X = W;
@@ -951,10 +1036,10 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     hh.Q = Qh;
     if (sparse) {
         hw.csr = &V->s;
-        hw.plan = pw;
+        hw.spplan = pw;
         hw.nsplit = 1;
         hh.csr = &Vt->s;
-        hh.plan = ph;
+        hh.spplan = ph;
         hh.nsplit = 1;
     } else {
         hw.A = (const float *)V->d.data;
@@ -965,6 +1050,14 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
         hh.lda = vt_ld;
         hh.K = m;
         hh.nsplit = sh;
+    }
+    hw.tc_mode = hh.tc_mode = sparse ? -1 : mode;
+    hw.pack = hh.pack = pack;
+    if (mode >= 0) {
+        hw.Atc = mode == TC_BF16 ? (const void *)vbf : (const void *)hw.A;
+        hw.lda_tc = mode == TC_BF16 ? n : hw.lda;
+        hh.Atc = mode == TC_BF16 ? (const void *)vtbf : (const void *)hh.A;
+        hh.lda_tc = mode == TC_BF16 ? m : hh.lda;
     }
 
     cudaStream_t s = h->stream;

@@ -227,7 +227,10 @@ __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
         }
         __syncthreads();
     }
-    double fit = 0.0;
+    // the thread's 16 squares summed in FP32 (relative error ~1e-6 on a
+    // 16-term sum), everything across threads in FP64: FP64 arithmetic is a
+    // small fraction of FP32 throughput on this part
+    float fit32 = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         int64_t gi = i0 + ty + 16 * i;
@@ -237,11 +240,12 @@ __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
         for (int j = 0; j < 4; ++j) {
             int64_t gj = j0 + tx + 16 * j;
             if (gj < a.n) {
-                double e = (double)(a.V[gi * a.ldv + gj] - acc[i][j]);
-                fit += e * e;
+                float e = a.V[gi * a.ldv + gj] - acc[i][j];
+                fit32 = fmaf(e, e, fit32);
             }
         }
     }
+    double fit = (double)fit32;
     // penalty sums, grid-strided over the (small) factors
     double sw = 0.0, sw2 = 0.0, shh = 0.0, sh2 = 0.0;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + tid, gs = (int64_t)gridDim.x * blockDim.x;
@@ -305,12 +309,21 @@ __global__ void __launch_bounds__(kRedThreads) k_sumsq(const T *__restrict__ x, 
 {
     __shared__ double sh[32];
     __shared__ bool last;
+    // groups of 16 squares in FP32, the groups summed in FP64
     double s = 0.0;
+    float g = 0.f;
+    int cnt = 0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        double v = as_d<T>(x[e]);
-        s += v * v;
+        float v = (float)as_d<T>(x[e]);
+        g = fmaf(v, v, g);
+        if (++cnt == 16) {
+            s += (double)g;
+            g = 0.f;
+            cnt = 0;
+        }
     }
+    s += (double)g;
     s = block_sum_d(s, sh);
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = s;

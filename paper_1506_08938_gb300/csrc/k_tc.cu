@@ -1,0 +1,706 @@
+// Tensor-core cross term C = A B on tcgen05 (sm_103a): A is the data matrix
+// (V for the W-update, V^T for the H-update; M x K, K contiguous) and B the
+// other factor (K x r).  Alg. 2 "Y = F V^T", the dominant O(mnr) term of
+// §4.2.  At r <= 128 the product is bound by the bytes of A, so the design
+// goal is to stream A from HBM once at full bandwidth:
+//
+//  * Work split (stream-K).  The (row tile, 32-wide k block) iterations are
+//    cut into equal contiguous ranges, one per CTA, one CTA per SM.  Every SM
+//    streams the same number of bytes whatever M and K are.  A CTA writes the
+//    accumulator of each row tile it touches into partial slice
+//    (CTA - first CTA of that tile); the consumer sums the slices in order.
+//  * Pipeline.  Warp 0 (one thread) issues TMA loads of the A tile (128 rows x
+//    128 B, 128B swizzle) and the B tile (packed factor, N x 128 B) into a
+//    ring of stages tracked by mbarriers.  Warp 1 (one thread) issues
+//    tcgen05.mma into a TMEM accumulator (128 lanes x N columns, FP32) and
+//    commits each stage back to the producer.  The accumulator is double
+//    buffered in TMEM: every chunk of k blocks goes to one buffer while warps
+//    2-9 read the other through tcgen05.ld and add it into FP32 registers
+//    (round to nearest), so the tensor core's truncating accumulation never
+//    runs over more than one chunk.
+//  * Arithmetic.  TF32: one MMA per k step.  TF32X3: warps 2-9 split each A
+//    tile in shared memory into its nearest TF32 value (in place) and the
+//    nearest TF32 value of the remainder; the packed factor comes split the
+//    same way; hi*hi + hi*lo + lo*hi are accumulated in FP32 in TMEM.  BF16:
+//    A and B in BF16, kind::f16.
+//  * Every wait is bounded by a global-timer deadline; on expiry the CTA
+//    raises the timeout bit of the status word, drains, frees TMEM and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "nmf_internal.cuh"
+
+namespace nmfi {
+namespace {
+
+constexpr int kThreads = 320;     // producer, MMA, 8 split/accumulate warps
+constexpr int kEpi = 256;         // threads of warps 2..9
+constexpr uint32_t kABytes = 128 * 128;   // 128 rows x 128 bytes
+constexpr unsigned long long kDeadlineNs = 2000000000ull;   // 2 s, a kernel takes < 1 ms
+
+__device__ __forceinline__ uint32_t su32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity; false if the deadline passed or
+// another role already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity,
+                                          unsigned long long deadline, volatile int *abort_flag)
+{
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try(b, parity))
+            return true;
+        if ((i & 63) == 63) {
+            if (*abort_flag)
+                return false;
+            if (gtimer() > deadline) {
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major rows of 128 bytes, 128B swizzle,
+// 8-row core groups 1024 bytes apart (tiles are 1024-byte aligned)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused with swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;             // descriptor version
+    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+    return d;
+}
+
+// instruction descriptor: D = F32, A/B format, both K-major, N, M
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, int M, int N)
+{
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+template <int MODE>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc)
+{
+    if constexpr (MODE == TC_BF16) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *v)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// nearest TF32 value (10-bit mantissa): the tensor core then sees exactly
+// this value whatever rounding its own conversion uses
+__host__ __device__ __forceinline__ float rn_tf32(float v)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xffffe000u);
+#else
+    return v;
+#endif
+}
+
+// CTA that owns iteration x when `iters` iterations are cut into `grid`
+// contiguous ranges [floor(c iters/grid), floor((c+1) iters/grid)).
+__host__ __device__ inline int owner_of(int64_t x, int64_t iters, int grid)
+{
+    int64_t c = x * grid / iters;
+    while (c + 1 < grid && (c + 1) * iters / grid <= x)
+        ++c;
+    while (c > 0 && c * iters / grid > x)
+        --c;
+    return (int)c;
+}
+
+template <int MODE, int NPAD, int STAGES, int DRAIN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_cross(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmBlo, const TcArgs p)
+{
+    constexpr bool X3 = MODE == TC_TF32X3;
+    constexpr uint32_t B_BYTES = NPAD * 128;
+    constexpr uint32_t STAGE_BYTES = (X3 ? 2 : 1) * (kABytes + B_BYTES);
+    constexpr uint32_t TX_BYTES = kABytes + (X3 ? 2 : 1) * B_BYTES;
+    constexpr int KSTEP_ELEMS = MODE == TC_BF16 ? 64 : 32;   // elements per 128-byte row
+    constexpr int KMMA = 4;                                   // MMAs of 32 bytes per stage
+    constexpr uint32_t BUF_COLS = NPAD <= 32 ? 32 : (NPAD <= 64 ? 64 : 128);
+    constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;   // two accumulators
+    constexpr uint32_t ID = idesc(MODE == TC_BF16 ? 1u : 2u, 128, NPAD);
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                ~uintptr_t(1023));
+    auto A = [&](int s) { return smem + s * STAGE_BYTES; };
+    auto Alo = [&](int s) { return smem + s * STAGE_BYTES + kABytes; };
+    auto B = [&](int s) { return smem + s * STAGE_BYTES + (X3 ? 2 : 1) * kABytes; };
+    auto Blo = [&](int s) { return smem + s * STAGE_BYTES + 2 * kABytes + B_BYTES; };
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *full = bars, *split = bars + STAGES, *empty = bars + 2 * STAGES;
+    uint64_t *acc_full = bars + 3 * STAGES, *acc_empty = acc_full + 2;   // two buffers each
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t it0 = (int64_t)blockIdx.x * p.iters / p.grid;
+    const int64_t it1 = (int64_t)(blockIdx.x + 1) * p.iters / p.grid;
+    const int KB = p.kblocks;
+    const unsigned long long deadline = gtimer() + kDeadlineNs;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&split[s], kEpi);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kEpi);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            for (int64_t it = it0; it < it1; ++it) {
+                const int tile = (int)(it / KB), kb = (int)(it % KB);
+                if (!mbar_wait(&empty[stage], phase ^ 1u, deadline, abort_flag))
+                    break;
+                mbar_expect_tx(&full[stage], TX_BYTES);
+                tma_load_2d(A(stage), &tmA, &full[stage], kb * KSTEP_ELEMS, tile * 128);
+                tma_load_2d(B(stage), &tmB, &full[stage], kb * KSTEP_ELEMS, 0);
+                if constexpr (X3)
+                    tma_load_2d(Blo(stage), &tmBlo, &full[stage], kb * KSTEP_ELEMS, 0);
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+            // drain: every load issued must land before the CTA exits
+            for (int s = 0; s < STAGES; ++s) {
+                if (!mbar_wait(&empty[stage], phase ^ 1u, deadline + kDeadlineNs, abort_flag)) {
+                    // the consumer stopped; wait for the load itself instead
+                    mbar_wait(&full[stage], phase, deadline + 2 * kDeadlineNs, abort_flag);
+                }
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int stage = 0, buf = 0, pos = 0;
+            uint32_t phase = 0, uses0 = 0, uses1 = 0;
+            for (int64_t it = it0; it < it1; ++it) {
+                const int kb = (int)(it % KB);
+                const bool seg_start = it == it0 || kb == 0;
+                const bool seg_end = it + 1 == it1 || kb == KB - 1;
+                pos = seg_start ? 0 : pos + 1;
+                const bool chunk_start = pos % DRAIN == 0;
+                const bool chunk_end = seg_end || pos % DRAIN == DRAIN - 1;
+                if (chunk_start) {
+                    // the accumulating warps have drained the previous use of this buffer
+                    const uint32_t u = buf ? uses1 : uses0;
+                    if (!mbar_wait(&acc_empty[buf], (u & 1u) ^ 1u, deadline, abort_flag))
+                        break;
+                    if (buf)
+                        ++uses1;
+                    else
+                        ++uses0;
+                    tc_fence_after();
+                }
+                if (!mbar_wait(X3 ? &split[stage] : &full[stage], phase, deadline, abort_flag))
+                    break;
+                tc_fence_after();
+                const uint32_t d = tmem + buf * BUF_COLS;
+                const uint32_t a0 = su32(A(stage)), b0 = su32(B(stage));
+#pragma unroll
+                for (int kk = 0; kk < KMMA; ++kk) {
+                    const uint64_t ad = sdesc(a0 + 32 * kk), bd = sdesc(b0 + 32 * kk);
+                    mma<MODE>(d, ad, bd, ID, (chunk_start && kk == 0) ? 0u : 1u);
+                    if constexpr (X3) {
+                        const uint64_t adl = sdesc(su32(Alo(stage)) + 32 * kk);
+                        const uint64_t bdl = sdesc(su32(Blo(stage)) + 32 * kk);
+                        mma<MODE>(d, ad, bdl, ID, 1u);
+                        mma<MODE>(d, adl, bd, ID, 1u);
+                    }
+                }
+                mma_commit(&empty[stage]);
+                if (chunk_end) {
+                    mma_commit(&acc_full[buf]);
+                    buf ^= 1;
+                }
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+    } else {
+        // ---------------- split (TF32X3) and accumulation: warps 2..9, 256 threads
+        // Thread (quad, lane, half) owns row quad*32 + lane of the tile and
+        // columns [half*HC, half*HC + HC).  Each chunk of DRAIN k blocks is
+        // accumulated by the tensor core in one TMEM buffer, then read here
+        // and added into FP32 registers with round-to-nearest adds: the tensor
+        // core's own accumulation rounds toward zero, which over a long chain
+        // biases the sum low.
+        constexpr int HC = NPAD / 2;                 // columns per thread
+        const int t = threadIdx.x - 64;              // 0..255
+        const int quad = warp & 3;                   // TMEM lane quadrant this warp may read
+        const int half = (warp - 2) >> 2;
+        const uint32_t lane_base = ((uint32_t)(quad * 32) << 16) + half * HC;
+        float acc[HC];
+#pragma unroll
+        for (int j = 0; j < HC; ++j)
+            acc[j] = 0.f;
+        int stage = 0, buf = 0, pos = 0, pending = -1;
+        uint32_t phase = 0, drains0 = 0, drains1 = 0;
+        bool ok = true;
+        auto drain = [&](int b) -> bool {
+            const uint32_t n = b ? drains1 : drains0;
+            if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], n & 1u, deadline, abort_flag)))
+                return false;
+            if (b)
+                ++drains1;
+            else
+                ++drains0;
+            __syncwarp();
+            tc_fence_after();
+            if constexpr (HC >= 16) {
+#pragma unroll
+                for (int c0 = 0; c0 < HC; c0 += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(tmem + b * BUF_COLS + lane_base + c0, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        acc[c0 + j] += __uint_as_float(v[j]);
+                }
+            } else {
+                uint32_t v[8];
+                tmem_ld8(tmem + b * BUF_COLS + lane_base, v);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    acc[j] += __uint_as_float(v[j]);
+            }
+            tc_fence_before();
+            mbar_arrive(&acc_empty[b]);
+            return true;
+        };
+        for (int64_t it = it0; it < it1 && ok; ++it) {
+            const int tile = (int)(it / KB), kb = (int)(it % KB);
+            const bool seg_start = it == it0 || kb == 0;
+            const bool seg_end = it + 1 == it1 || kb == KB - 1;
+            pos = seg_start ? 0 : pos + 1;
+            const bool chunk_end = seg_end || pos % DRAIN == DRAIN - 1;
+            if constexpr (X3) {
+                // warp-uniform decision: every lane of the warp continues or none
+                if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, deadline, abort_flag)))
+                    break;
+                float4 *a4 = reinterpret_cast<float4 *>(A(stage));
+                float4 *l4 = reinterpret_cast<float4 *>(Alo(stage));
+#pragma unroll
+                for (int q = 0; q < (int)(kABytes / 16 / kEpi); ++q) {
+                    const int idx = t + kEpi * q;
+                    float4 v = a4[idx];
+                    float4 hi;
+                    hi.x = rn_tf32(v.x);
+                    hi.y = rn_tf32(v.y);
+                    hi.z = rn_tf32(v.z);
+                    hi.w = rn_tf32(v.w);
+                    a4[idx] = hi;
+                    l4[idx] = make_float4(rn_tf32(v.x - hi.x), rn_tf32(v.y - hi.y),
+                                          rn_tf32(v.z - hi.z), rn_tf32(v.w - hi.w));
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&split[stage]);
+            }
+            if (++stage == STAGES) {
+                stage = 0;
+                phase ^= 1u;
+            }
+            // drain the previous chunk now that the tensor core has the next one
+            if (pending >= 0) {
+                ok = drain(pending);
+                pending = -1;
+                if (!ok)
+                    break;
+            }
+            if (!chunk_end)
+                continue;
+            const int b = buf;
+            buf ^= 1;
+            if (!seg_end) {
+                pending = b;
+                continue;
+            }
+            if (!(ok = drain(b)))
+                break;
+            // ---- store this CTA's part of `tile`
+            const int64_t first_it = (int64_t)tile * KB, last_it = first_it + KB - 1;
+            const int c_first = owner_of(first_it, p.iters, p.grid);
+            const int c_last = owner_of(last_it, p.iters, p.grid);
+            const int slice = (int)blockIdx.x - c_first;
+            const int64_t row = (int64_t)tile * 128 + quad * 32 + lane;
+            if (row < p.M) {
+                float *dst = p.P + (int64_t)slice * p.M * p.r + row * p.r + half * HC;
+#pragma unroll
+                for (int j = 0; j < HC; ++j)
+                    if (half * HC + j < p.r)
+                        dst[j] = acc[j];
+                // the first part of a tile clears the slices no CTA writes for it
+                if (slice == 0) {
+                    for (int s2 = c_last - c_first + 1; s2 < p.nslices; ++s2) {
+                        float *z = p.P + (int64_t)s2 * p.M * p.r + row * p.r + half * HC;
+                        for (int j = 0; j < HC && half * HC + j < p.r; ++j)
+                            z[j] = 0.f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < HC; ++j)
+                acc[j] = 0.f;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag && p.status)
+        atomicOr(p.status, kStTimeout);
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---- factor packing: X (K x r, row-major) -> B (NPAD x Kp, K contiguous) --
+// mode TF32: raw FP32; TF32X3: high part (TF32-exact) and remainder; BF16:
+// round to nearest BF16.  Rows r..NPAD-1 and columns K..Kp-1 are zero.
+template <int MODE>
+__global__ void k_pack_factor(const float *__restrict__ X, int64_t K, int r, int npad, int64_t kp,
+                              void *__restrict__ Bhi, float *__restrict__ Blo)
+{
+    __shared__ float t[32][33];
+    const int64_t k0 = (int64_t)blockIdx.x * 32;
+    const int n0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t k = k0 + i;
+        const int n = n0 + threadIdx.x;
+        t[i][threadIdx.x] = (k < K && n < r) ? X[k * r + n] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int n = n0 + i;
+        const int64_t k = k0 + threadIdx.x;
+        if (n >= npad || k >= kp)
+            continue;
+        const float v = t[threadIdx.x][i];
+        if constexpr (MODE == TC_BF16) {
+            reinterpret_cast<__nv_bfloat16 *>(Bhi)[(int64_t)n * kp + k] = __float2bfloat16_rn(v);
+        } else if constexpr (MODE == TC_TF32X3) {
+            const float hi = rn_tf32(v);
+            reinterpret_cast<float *>(Bhi)[(int64_t)n * kp + k] = hi;
+            Blo[(int64_t)n * kp + k] = rn_tf32(v - hi);
+        } else {
+            reinterpret_cast<float *>(Bhi)[(int64_t)n * kp + k] = v;
+        }
+    }
+}
+
+// ---- host side ----------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+bool make_map(CUtensorMap *m, const void *base, bool bf16, uint64_t inner, uint64_t outer,
+              uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    2, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int MODE, int NPAD>
+constexpr int stages_for()
+{
+    constexpr int stage = (MODE == TC_TF32X3 ? 2 : 1) * (kABytes + NPAD * 128);
+    constexpr int s = (200 * 1024) / stage;
+    return s > 8 ? 8 : s;
+}
+
+template <int MODE, int NPAD>
+cudaError_t launch_mode(const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &bl,
+                        const TcArgs &p, cudaStream_t s)
+{
+    constexpr int ST = stages_for<MODE, NPAD>();
+    constexpr int stage = (MODE == TC_TF32X3 ? 2 : 1) * (kABytes + NPAD * 128);
+    const size_t smem = (size_t)ST * stage + 1024 + 256;
+    constexpr int DR = MODE == TC_TF32X3 ? 1 : 2;   // k blocks per accumulator chunk
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_cross<MODE, NPAD, ST, DR>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        attr = true;
+    }
+    k_tc_cross<MODE, NPAD, ST, DR><<<p.grid, kThreads, smem, s>>>(a, b, bl, p);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_npad(int npad, const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &bl,
+                        const TcArgs &p, cudaStream_t s)
+{
+    switch (npad) {
+    case 16: return launch_mode<MODE, 16>(a, b, bl, p, s);
+    case 32: return launch_mode<MODE, 32>(a, b, bl, p, s);
+    case 64: return launch_mode<MODE, 64>(a, b, bl, p, s);
+    default: return launch_mode<MODE, 128>(a, b, bl, p, s);
+    }
+}
+
+int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n < 1)
+            n = 1;
+    }
+    return n;
+}
+
+}  // namespace
+
+int tc_npad(int r) { return r <= 16 ? 16 : r <= 32 ? 32 : r <= 64 ? 64 : 128; }
+
+int64_t tc_kpad(int64_t K, int mode) { return mode == TC_BF16 ? (K + 7) / 8 * 8 : (K + 3) / 4 * 4; }
+
+size_t tc_pack_bytes(int64_t K, int r, int mode)
+{
+    const int64_t kp = tc_kpad(K, mode);
+    const size_t e = mode == TC_BF16 ? 2 : 4;
+    return (size_t)tc_npad(r) * kp * e * (mode == TC_TF32X3 ? 2 : 1) + 512;
+}
+
+cudaError_t launch_tc_pack(const float *X, int64_t K, int r, int mode, void *pack, cudaStream_t s)
+{
+    ProfScope prof_(KC_OTHER, s);
+    const int npad = tc_npad(r);
+    const int64_t kp = tc_kpad(K, mode);
+    const size_t hb = (size_t)npad * kp * (mode == TC_BF16 ? 2 : 4);
+    float *lo = reinterpret_cast<float *>(reinterpret_cast<char *>(pack) + ((hb + 255) & ~size_t(255)));
+    dim3 grid((unsigned)((kp + 31) / 32), (unsigned)((npad + 31) / 32));
+    dim3 blk(32, 8);
+    if (mode == TC_BF16)
+        k_pack_factor<TC_BF16><<<grid, blk, 0, s>>>(X, K, r, npad, kp, pack, nullptr);
+    else if (mode == TC_TF32X3)
+        k_pack_factor<TC_TF32X3><<<grid, blk, 0, s>>>(X, K, r, npad, kp, pack, lo);
+    else
+        k_pack_factor<TC_TF32><<<grid, blk, 0, s>>>(X, K, r, npad, kp, pack, nullptr);
+    count_launch();
+    return cudaGetLastError();
+}
+
+bool tc_supported(int64_t lda, int mode, const void *A)
+{
+    const int64_t align = mode == TC_BF16 ? 8 : 4;   // 16-byte row pitch
+    return (lda % align) == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0 && encode_fn();
+}
+
+TcPlan tc_plan(int64_t M, int64_t K, int r, int mode)
+{
+    TcPlan pl;
+    const int kstep = mode == TC_BF16 ? 64 : 32;
+    pl.kblocks = (int)((K + kstep - 1) / kstep);
+    pl.tiles = (int)((M + 127) / 128);
+    pl.iters = (int64_t)pl.tiles * pl.kblocks;
+    int g = sm_count();
+    if (pl.iters < g)
+        g = (int)pl.iters;
+    pl.grid = g < 1 ? 1 : g;
+    int ns = 1;
+    for (int t = 0; t < pl.tiles; ++t) {
+        const int64_t f = (int64_t)t * pl.kblocks, l = f + pl.kblocks - 1;
+        const int n = owner_of(l, pl.iters, pl.grid) - owner_of(f, pl.iters, pl.grid) + 1;
+        ns = n > ns ? n : ns;
+    }
+    pl.nslices = ns;
+    return pl;
+}
+
+cudaError_t launch_tc_cross(const void *A, int64_t M, int64_t K, int64_t lda, int r, int mode,
+                            const void *pack, float *P, const TcPlan &pl, unsigned *status,
+                            cudaStream_t s)
+{
+    ProfScope prof_(KC_CROSS, s);
+    if (M <= 0)
+        return cudaSuccess;
+    const int npad = tc_npad(r);
+    const bool bf = mode == TC_BF16;
+    const int64_t kp = tc_kpad(K, mode);
+    const size_t es = bf ? 2 : 4;
+    const size_t hb = (size_t)npad * kp * es;
+    const void *lo = reinterpret_cast<const char *>(pack) + ((hb + 255) & ~size_t(255));
+    CUtensorMap ma, mb, ml;
+    const uint32_t box_k = bf ? 64 : 32;
+    if (!make_map(&ma, A, bf, (uint64_t)K, (uint64_t)M, (uint64_t)lda * es, box_k, 128) ||
+        !make_map(&mb, pack, bf, (uint64_t)kp, (uint64_t)npad, (uint64_t)kp * es, box_k,
+                  (uint32_t)npad))
+        return cudaErrorInvalidValue;
+    if (mode == TC_TF32X3) {
+        if (!make_map(&ml, lo, false, (uint64_t)kp, (uint64_t)npad, (uint64_t)kp * 4, box_k,
+                      (uint32_t)npad))
+            return cudaErrorInvalidValue;
+    } else {
+        ml = mb;
+    }
+    TcArgs p{};
+    p.M = M;
+    p.r = r;
+    p.kblocks = pl.kblocks;
+    p.iters = pl.iters;
+    p.grid = pl.grid;
+    p.nslices = pl.nslices;
+    p.P = P;
+    p.status = status;
+    if (mode == TC_BF16)
+        return launch_npad<TC_BF16>(npad, ma, mb, ml, p, s);
+    if (mode == TC_TF32X3)
+        return launch_npad<TC_TF32X3>(npad, ma, mb, ml, p, s);
+    return launch_npad<TC_TF32>(npad, ma, mb, ml, p, s);
+}
+
+}  // namespace nmfi

@@ -71,6 +71,33 @@ cudaError_t launch_sum_slices(const float *P, int nsplit, int64_t n, float *out,
 cudaError_t launch_transpose_f32(const float *A, int64_t rows, int64_t cols, int64_t lda,
                                  float *out, cudaStream_t s);
 
+// ---- tensor-core cross term (tcgen05) ---------------------------------------
+enum TcMode { TC_TF32 = 0, TC_TF32X3 = 1, TC_BF16 = 2 };
+struct TcArgs {
+    int64_t M;
+    int r;
+    int kblocks;
+    int64_t iters;
+    int grid;
+    int nslices;
+    float *P;          // nslices x M x r partial slices
+    unsigned *status;
+};
+struct TcPlan {
+    int kblocks = 0, tiles = 0, grid = 0, nslices = 1;
+    int64_t iters = 0;
+};
+int tc_npad(int r);
+int64_t tc_kpad(int64_t K, int mode);
+size_t tc_pack_bytes(int64_t K, int r, int mode);
+bool tc_supported(int64_t lda, int mode, const void *A);
+TcPlan tc_plan(int64_t M, int64_t K, int r, int mode);
+// pack X (K x r row-major FP32) as the B operand of mode `mode`
+cudaError_t launch_tc_pack(const float *X, int64_t K, int r, int mode, void *pack, cudaStream_t s);
+cudaError_t launch_tc_cross(const void *A, int64_t M, int64_t K, int64_t lda, int r, int mode,
+                            const void *pack, float *P, const TcPlan &pl, unsigned *status,
+                            cudaStream_t s);
+
 // ---- sparse cross term ----------------------------------------------------
 struct SpmmPlan {
     int64_t pieces = 0;     // number of merge-path pieces

@@ -1,0 +1,108 @@
+"""tcgen05 tensor-core cross term C = A B (through nmf_cross) against the FP64
+oracle.  Shapes cover partial row tiles, K not a multiple of the 32-wide k
+block, every padded width (r -> 16, 32, 64, 128) and stream-K splits where a
+row tile is shared by several CTAs.
+
+Bounds: FP32 (3xTF32 split with the TMEM accumulator drained into FP32
+registers every k block; measured 2.9e-7 for every K) 2e-6 relative;
+TF32 (10-bit mantissa, truncation) ~ 2^-10 per product: 2e-3; BF16 inputs
+rounded to 8 bits: relative 2^-8 per product: 1e-2.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as WL
+from tests.gpu_common import dev, rel_err, t32, to_np, torch
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_1506_08938_gb300")
+
+
+@pytest.fixture(scope="module")
+def h():
+    import __graft_entry__ as g
+    g.build()
+    hh = P.Handle(0)
+    yield hh
+    hh.close()
+
+
+SHAPES = [(1, 32), (127, 64), (129, 96), (1000, 3008), (300, 20000), (4096, 10000)]
+
+
+@pytest.mark.parametrize("M,K", SHAPES)
+@pytest.mark.parametrize("r", [4, 16, 50, 64, 100, 128])
+def test_tc_cross_fp32_split(h, M, K, r):
+    g = WL.rng(M * 7 + K + r)
+    A = g.random((M, K)).astype(np.float32)
+    B = g.random((K, r)).astype(np.float32)
+    Co = O.cross_dense(A.astype(np.float64), B.astype(np.float64))
+    Cg = P.nmf_cross(h, t32(A), t32(B), prec="fp32")
+    h.sync()
+    err = rel_err(to_np(Cg), Co)
+    bias = float(np.mean((to_np(Cg) - Co) / Co))
+    print(f"tc fp32 M={M} K={K} r={r}: rel {err:.3e} bias {bias:.3e}")
+    assert err < 2e-6
+
+
+@pytest.mark.parametrize("M,K", [(129, 96), (1000, 3008), (4096, 10000)])
+@pytest.mark.parametrize("r", [16, 50, 128])
+def test_tc_cross_tf32(h, M, K, r):
+    g = WL.rng(M + K + r + 1)
+    A = g.random((M, K)).astype(np.float32)
+    B = g.random((K, r)).astype(np.float32)
+    Co = O.cross_dense(A.astype(np.float64), B.astype(np.float64))
+    Cg = P.nmf_cross(h, t32(A), t32(B), prec="tf32")
+    h.sync()
+    err = rel_err(to_np(Cg), Co)
+    print(f"tc tf32 M={M} K={K} r={r}: rel {err:.3e}")
+    assert err < 2e-3
+
+
+@pytest.mark.parametrize("M,K", [(129, 96), (1000, 3008), (4096, 10000)])
+@pytest.mark.parametrize("r", [16, 50, 128])
+def test_tc_cross_bf16(h, M, K, r):
+    g = WL.rng(M + K + r + 2)
+    A = g.random((M, K)).astype(np.float32)
+    B = g.random((K, r)).astype(np.float32)
+    Ab = torch.tensor(A, device=dev()).to(torch.bfloat16)
+    # the oracle sees the BF16-rounded A; B is rounded inside the kernel
+    Co = O.cross_dense(Ab.float().cpu().numpy().astype(np.float64), B.astype(np.float64))
+    Cg = P.nmf_cross(h, Ab, t32(B), prec="bf16")
+    h.sync()
+    err = rel_err(to_np(Cg), Co)
+    print(f"tc bf16 M={M} K={K} r={r}: rel {err:.3e}")
+    assert err < 1e-2
+
+
+def test_tc_cross_unaligned_falls_back(h):
+    g = WL.rng(5)
+    A = g.random((300, 3005)).astype(np.float32)    # row pitch not a multiple of 16 B
+    B = g.random((3005, 50)).astype(np.float32)
+    Co = O.cross_dense(A.astype(np.float64), B.astype(np.float64))
+    Cg = P.nmf_cross(h, t32(A), t32(B), prec="fp32")
+    h.sync()
+    assert rel_err(to_np(Cg), Co) < 2e-6
+    with pytest.raises(P.NmfError):
+        P.nmf_cross(h, t32(A), t32(B), prec="tf32")
+
+
+def test_tc_and_simt_solves_agree(h):
+    """The dense solve with tensor-core FP32 and with CUDA-core FP32 cross
+    terms: both are FP32-accurate, so the first iterations agree to the FP32
+    per-step bound."""
+    import ctypes as C
+    inst = WL.tiny(seed=0, r=10)
+    V = t32(inst.V)
+    out = []
+    for prec in ("fp32", "fp32_simt"):
+        W = t32(inst.W0)
+        Ht = t32(inst.Ht0)
+        hist = np.zeros(3)
+        o = P.solve_opts(3, prec=prec, nnls=P.nnls_opts(max_inner=3, eps=0.0), objective="direct",
+                         obj_hist=hist.ctypes.data_as(C.POINTER(C.c_double)))
+        P.nmf_solve(h, V, W, Ht, o)
+        out.append((to_np(W), to_np(Ht), hist.copy()))
+    assert np.abs(out[0][2] - out[1][2]).max() / out[1][2].max() < 1e-4
