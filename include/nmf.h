@@ -120,7 +120,9 @@ typedef struct {
     float beta_w, beta_h;    /* L2 weights (added to the Gram diagonal)        */
     nmf_prec prec;           /* product arithmetic                            */
     nmf_nnls_opts nnls;
-    int check_every;         /* gap test period in iterations (0 = 1)         */
+    int check_every;         /* gap test period in iterations (0 = 1); < 0:
+                                adaptive - the next test is scheduled from
+                                the gap's measured rate of decrease         */
     int use_graph;           /* 1: capture one iteration as a CUDA graph       */
     int objective;           /* how J is evaluated after each iteration:
                                 0 = FP64 trace identity (cheap; its FP32 inputs

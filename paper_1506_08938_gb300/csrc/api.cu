@@ -1084,7 +1084,15 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
         return st;
 
     const bool gap_on = o.rel_gap_target > 0.0 && o.f_star > 0.0;
+    const bool adaptive = o.check_every < 0;
     const int check = o.check_every > 0 ? o.check_every : 1;
+    // adaptive gap tests: from the last two tests estimate the iterations
+    // still needed (gap falls roughly linearly over a few dozen iterations)
+    // and test again after about half of them
+    int next_check = adaptive ? 4 : check;
+    int prev_t = -1;
+    double prev_gap = 0.0;
+    int n_checks = 0;
     std::vector<double> hist;
     int done_iters = 0;
     double Jlast = NAN;
@@ -1130,7 +1138,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
         }
         ++done_iters;
         const bool last = t + 1 == o.outer_iters;
-        const bool check_now = gap_on && (((t + 1) % check == 0) || last);
+        const bool check_now = gap_on && (t + 1 >= next_check || last);
         if (o.obj_hist || check_now || (last && rep)) {
             if ((st = enqueue_objective(h, L, o, o.f_star, o.rel_gap_target)))
                 return st;
@@ -1143,8 +1151,26 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
             if (o.obj_hist)
                 o.obj_hist[t] = J;
             Jlast = J;
-            if (gap_on && (J - o.f_star) / o.f_star <= o.rel_gap_target)
-                break;
+            if (check_now) {
+                ++n_checks;
+                const double gap = (J - o.f_star) / o.f_star;
+                if (gap <= o.rel_gap_target)
+                    break;
+                if (adaptive) {
+                    int step = 16;
+                    if (prev_t >= 0 && prev_gap > gap) {
+                        const double rate = (prev_gap - gap) / (double)(t - prev_t);
+                        const double need = (gap - o.rel_gap_target) / rate;
+                        step = (int)(0.5 * need);
+                    }
+                    step = step < 1 ? 1 : (step > 64 ? 64 : step);
+                    prev_t = t;
+                    prev_gap = gap;
+                    next_check = t + 1 + step;
+                } else {
+                    next_check = t + 1 + check;
+                }
+            }
         }
     }
     if (!have_j && rep && done_iters > 0) {

@@ -136,16 +136,37 @@ __global__ void __launch_bounds__(kThreads) k_gram_f32(const float *__restrict__
         }
 }
 
-// out[e] = sum_s P[s * n + e], s ascending (fixed order => reproducible)
-__global__ void k_sum_slices(const float *__restrict__ P, int nsplit, int64_t n,
-                             float *__restrict__ out)
+// out[e] = sum_s P[s * n + e].  A block covers 32 consecutive elements; its 8
+// warps take interleaved slices (w, w + 8, ...) with coalesced 128-byte loads,
+// then warp 0 adds the 8 warp sums in order: a fixed order, so the result is
+// reproducible, with 8 x the loads in flight of one thread per element.
+__global__ void __launch_bounds__(256) k_sum_slices(const float *__restrict__ P, int nsplit,
+                                                    int64_t n, float *__restrict__ out)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int k = 0; k < nsplit; ++k)
-            s += P[k * n + e];
-        out[e] = s;
+    __shared__ float part[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t e0 = (int64_t)blockIdx.x * 32; e0 < n; e0 += (int64_t)gridDim.x * 32) {
+        const int64_t e = e0 + lane;
+        float a0 = 0.f, a1 = 0.f;
+        if (e < n) {
+            int k = w;
+            for (; k + 8 < nsplit; k += 16) {
+                a0 += P[(int64_t)k * n + e];
+                a1 += P[(int64_t)(k + 8) * n + e];
+            }
+            if (k < nsplit)
+                a0 += P[(int64_t)k * n + e];
+        }
+        part[w][lane] = a0 + a1;
+        __syncthreads();
+        if (w == 0 && e < n) {
+            float s = 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                s += part[q][lane];
+            out[e] = s;
+        }
+        __syncthreads();
     }
 }
 
@@ -183,7 +204,8 @@ int num_sms()
 
 int gram_splits(int64_t rows)
 {
-    int64_t s = rows / 256;
+    // 64 rows per CTA: every SM gets work even for K of a few thousand
+    int64_t s = (rows + 63) / 64;
     int64_t cap = 2 * (int64_t)num_sms();
     if (s > cap)
         s = cap;
@@ -259,9 +281,9 @@ cudaError_t launch_sum_slices(const float *P, int nsplit, int64_t n, float *out,
     ProfScope prof_(KC_OTHER, s);
     if (n <= 0)
         return cudaSuccess;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 4096)
-        blocks = 4096;
+    int64_t blocks = (n + 31) / 32;
+    if (blocks > 8192)
+        blocks = 8192;
     k_sum_slices<<<(unsigned)blocks, 256, 0, s>>>(P, nsplit, n, out);
     count_launch();
     return cudaGetLastError();

@@ -181,10 +181,11 @@ __global__ void __launch_bounds__(256) k_kkt(const float *__restrict__ Q,
 }
 
 // J = 1/2 sum_ij (V_ij - W_i . Ht_j)^2 + penalties, the residual formed
-// element by element: W_i . Ht_j by an FP32 fma chain over r, the square
-// accumulated in FP64.  Avoids the cancellation of the trace identity.  CTA
-// tile 64 x 64 of V, k-chunks of 32 of the factors staged in shared memory;
-// thread (ty, tx) owns rows ty + 16 i and columns tx + 16 j (i, j < 4).
+// element by element: W_i . Ht_j by an FP32 fma chain over r, its square
+// summed in FP32 over the thread's 16 elements of a 64 x 64 tile, the tile
+// sums in FP64.  Avoids the cancellation of the trace identity.  Persistent
+// CTAs walk the tiles; FP64 arithmetic (a small fraction of FP32 throughput
+// on this part) is kept to one add per thread per tile.
 __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
 {
     constexpr int BT = 64, KC = 32;
@@ -194,70 +195,94 @@ __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
     __shared__ bool last;
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     const int64_t tiles_n = (a.n + BT - 1) / BT;
-    const int64_t i0 = (blockIdx.x / tiles_n) * BT, j0 = (blockIdx.x % tiles_n) * BT;
-    float acc[4][4];
+    const int64_t tiles = ((a.m + BT - 1) / BT) * tiles_n;
+    double fit = 0.0;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t i0 = (tile / tiles_n) * BT, j0 = (tile % tiles_n) * BT;
+        float acc[4][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            acc[i][j] = 0.f;
-    for (int k0 = 0; k0 < a.r; k0 += KC) {
-        for (int idx = tid; idx < BT * KC; idx += 256) {
-            int rr = idx / KC, kk = idx - rr * KC;
-            int64_t gi = i0 + rr, gj = j0 + rr;
-            int gk = k0 + kk;
-            Ws[kk][rr] = (gi < a.m && gk < a.r) ? a.W[gi * a.r + gk] : 0.f;
-            Hs[kk][rr] = (gj < a.n && gk < a.r) ? a.Ht[gj * a.r + gk] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < KC; ++kk) {
-            float w[4], hh[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                w[i] = Ws[kk][ty + 16 * i];
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                hh[j] = Hs[kk][tx + 16 * j];
+                acc[i][j] = 0.f;
+        for (int k0 = 0; k0 < a.r; k0 += KC) {
+            __syncthreads();
+            for (int idx = tid; idx < BT * KC; idx += 256) {
+                int rr = idx / KC, kk = idx - rr * KC;
+                int64_t gi = i0 + rr, gj = j0 + rr;
+                int gk = k0 + kk;
+                Ws[kk][rr] = (gi < a.m && gk < a.r) ? a.W[gi * a.r + gk] : 0.f;
+                Hs[kk][rr] = (gj < a.n && gk < a.r) ? a.Ht[gj * a.r + gk] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < KC; ++kk) {
+                float w[4], hh[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i)
+                    w[i] = Ws[kk][ty + 16 * i];
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    acc[i][j] = fmaf(w[i], hh[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-    // the thread's 16 squares summed in FP32 (relative error ~1e-6 on a
-    // 16-term sum), everything across threads in FP64: FP64 arithmetic is a
-    // small fraction of FP32 throughput on this part
-    float fit32 = 0.f;
+                    hh[j] = Hs[kk][tx + 16 * j];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int64_t gi = i0 + ty + 16 * i;
-        if (gi >= a.m)
-            continue;
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int64_t gj = j0 + tx + 16 * j;
-            if (gj < a.n) {
-                float e = a.V[gi * a.ldv + gj] - acc[i][j];
-                fit32 = fmaf(e, e, fit32);
+                    for (int j = 0; j < 4; ++j)
+                        acc[i][j] = fmaf(w[i], hh[j], acc[i][j]);
             }
         }
+        float f32 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int64_t gi = i0 + ty + 16 * i;
+            if (gi >= a.m)
+                continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                int64_t gj = j0 + tx + 16 * j;
+                if (gj < a.n) {
+                    float e = a.V[gi * a.ldv + gj] - acc[i][j];
+                    f32 = fmaf(e, e, f32);
+                }
+            }
+        }
+        fit += (double)f32;
     }
-    double fit = (double)fit32;
-    // penalty sums, grid-strided over the (small) factors
+    // penalty sums over the factors: FP32 groups of 16, FP64 across groups
     double sw = 0.0, sw2 = 0.0, shh = 0.0, sh2 = 0.0;
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + tid, gs = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = gt; e < a.m * a.r; e += gs) {
-        double v = a.W[e];
-        sw += v;
-        sw2 += v * v;
-    }
-    for (int64_t e = gt; e < a.n * a.r; e += gs) {
-        double v = a.Ht[e];
-        shh += v;
-        sh2 += v * v;
+    {
+        const int64_t gt = (int64_t)blockIdx.x * blockDim.x + tid,
+                      gs = (int64_t)gridDim.x * blockDim.x;
+        float g1 = 0.f, g2 = 0.f;
+        int c = 0;
+        for (int64_t e = gt; e < a.m * a.r; e += gs) {
+            float v = a.W[e];
+            g1 += v;
+            g2 = fmaf(v, v, g2);
+            if (++c == 16) {
+                sw += g1;
+                sw2 += g2;
+                g1 = g2 = 0.f;
+                c = 0;
+            }
+        }
+        sw += g1;
+        sw2 += g2;
+        g1 = g2 = 0.f;
+        c = 0;
+        for (int64_t e = gt; e < a.n * a.r; e += gs) {
+            float v = a.Ht[e];
+            g1 += v;
+            g2 = fmaf(v, v, g2);
+            if (++c == 16) {
+                shh += g1;
+                sh2 += g2;
+                g1 = g2 = 0.f;
+                c = 0;
+            }
+        }
+        shh += g1;
+        sh2 += g2;
     }
     double v[5] = {fit, sw, sw2, shh, sh2};
 #pragma unroll
@@ -274,8 +299,6 @@ __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
     if (!last)
         return;
     __threadfence();
-    // last block: thread t sums blocks t, t + 256, ... (fixed order), then
-    // the block tree - the same grouping on every run
     volatile double *pp = a.partials;
     double t[5] = {0, 0, 0, 0, 0};
     for (unsigned b = tid; b < gridDim.x; b += blockDim.x)
@@ -293,14 +316,11 @@ __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
 }
 
 template <typename T>
-__device__ __forceinline__ double as_d(T v);
+__device__ __forceinline__ float as_f(T v);
 template <>
-__device__ __forceinline__ double as_d<float>(float v) { return (double)v; }
+__device__ __forceinline__ float as_f<float>(float v) { return v; }
 template <>
-__device__ __forceinline__ double as_d<__nv_bfloat16>(__nv_bfloat16 v)
-{
-    return (double)__bfloat162float(v);
-}
+__device__ __forceinline__ float as_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_sumsq(const T *__restrict__ x, int64_t n,
@@ -315,7 +335,7 @@ __global__ void __launch_bounds__(kRedThreads) k_sumsq(const T *__restrict__ x, 
     int cnt = 0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        float v = (float)as_d<T>(x[e]);
+        float v = as_f<T>(x[e]);
         g = fmaf(v, v, g);
         if (++cnt == 16) {
             s += (double)g;
@@ -368,18 +388,17 @@ cudaError_t launch_objective(const ObjArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-size_t objective_direct_partials(int64_t m, int64_t n)
-{
-    return (size_t)((m + 63) / 64) * (size_t)((n + 63) / 64) * 5;
-}
+constexpr int kObjBlocks = 4 * 152;   // persistent CTAs of the direct objective
+
+size_t objective_direct_partials(int64_t, int64_t) { return (size_t)kObjBlocks * 5; }
 
 cudaError_t launch_objective_direct(const ObjDirectArgs &a, cudaStream_t s)
 {
     ProfScope prof_(KC_OBJECTIVE, s);
     const int64_t tiles = ((a.m + 63) / 64) * ((a.n + 63) / 64);
-    if (tiles <= 0 || tiles > 0x7fffffff)
+    if (tiles <= 0)
         return cudaErrorInvalidValue;
-    k_objective_direct<<<(unsigned)tiles, 256, 0, s>>>(a);
+    k_objective_direct<<<(unsigned)(tiles < kObjBlocks ? tiles : kObjBlocks), 256, 0, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }

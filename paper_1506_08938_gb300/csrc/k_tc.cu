@@ -18,11 +18,13 @@
 //    2-9 read the other through tcgen05.ld and add it into FP32 registers
 //    (round to nearest), so the tensor core's truncating accumulation never
 //    runs over more than one chunk.
-//  * Arithmetic.  TF32: one MMA per k step.  TF32X3: warps 2-9 split each A
-//    tile in shared memory into its nearest TF32 value (in place) and the
-//    nearest TF32 value of the remainder; the packed factor comes split the
-//    same way; hi*hi + hi*lo + lo*hi are accumulated in FP32 in TMEM.  BF16:
-//    A and B in BF16, kind::f16.
+//  * Arithmetic.  TF32: one MMA per k step.  TF32X3 (FP32-accurate): the
+//    tensor core's TF32 conversion truncates, so the A tile serves as its own
+//    high part and warps 2-9 write the TF32-rounded remainder A - trunc(A)
+//    to a small ring; the packed factor stacks its TF32 high part over its
+//    TF32 remainder, so one N = 2 NPAD MMA gives A*B_hi and A*B_lo side by
+//    side in TMEM and a second (N = NPAD) adds A_lo*B_hi.  BF16: A and B in
+//    BF16, kind::f16.
 //  * Every wait is bounded by a global-timer deadline; on expiry the CTA
 //    raises the timeout bit of the status word, drains, frees TMEM and exits.
 #include <cuda.h>
@@ -200,31 +202,33 @@ __host__ __device__ inline int owner_of(int64_t x, int64_t iters, int grid)
     return (int)c;
 }
 
-template <int MODE, int NPAD, int STAGES, int DRAIN>
+template <int MODE, int NPAD, int STAGES, int NLO, int DRAIN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_cross(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const __grid_constant__ CUtensorMap tmBlo, const TcArgs p)
+               const TcArgs p)
 {
     constexpr bool X3 = MODE == TC_TF32X3;
-    constexpr uint32_t B_BYTES = NPAD * 128;
-    constexpr uint32_t STAGE_BYTES = (X3 ? 2 : 1) * (kABytes + B_BYTES);
-    constexpr uint32_t TX_BYTES = kABytes + (X3 ? 2 : 1) * B_BYTES;
+    constexpr int NB = X3 ? 2 * NPAD : NPAD;                  // rows of the packed factor tile
+    constexpr uint32_t B_BYTES = NB * 128;
+    constexpr uint32_t STAGE_BYTES = kABytes + B_BYTES;
+    constexpr uint32_t TX_BYTES = kABytes + B_BYTES;
     constexpr int KSTEP_ELEMS = MODE == TC_BF16 ? 64 : 32;   // elements per 128-byte row
     constexpr int KMMA = 4;                                   // MMAs of 32 bytes per stage
-    constexpr uint32_t BUF_COLS = NPAD <= 32 ? 32 : (NPAD <= 64 ? 64 : 128);
+    constexpr uint32_t BUF_COLS = NB <= 32 ? 32 : (NB <= 64 ? 64 : (NB <= 128 ? 128 : 256));
     constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;   // two accumulators
-    constexpr uint32_t ID = idesc(MODE == TC_BF16 ? 1u : 2u, 128, NPAD);
+    constexpr uint32_t ID_B = idesc(MODE == TC_BF16 ? 1u : 2u, 128, NB);     // A x packed tile
+    constexpr uint32_t ID_HI = idesc(2u, 128, NPAD);                         // A_lo x B_hi
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                 ~uintptr_t(1023));
     auto A = [&](int s) { return smem + s * STAGE_BYTES; };
-    auto Alo = [&](int s) { return smem + s * STAGE_BYTES + kABytes; };
-    auto B = [&](int s) { return smem + s * STAGE_BYTES + (X3 ? 2 : 1) * kABytes; };
-    auto Blo = [&](int s) { return smem + s * STAGE_BYTES + 2 * kABytes + B_BYTES; };
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
-    uint64_t *full = bars, *split = bars + STAGES, *empty = bars + 2 * STAGES;
-    uint64_t *acc_full = bars + 3 * STAGES, *acc_empty = acc_full + 2;   // two buffers each
+    auto B = [&](int s) { return smem + s * STAGE_BYTES + kABytes; };
+    auto LO = [&](int j) { return smem + STAGES * STAGE_BYTES + j * kABytes; };
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES + NLO * kABytes);
+    uint64_t *full = bars, *empty = bars + STAGES;
+    uint64_t *lo_full = bars + 2 * STAGES, *lo_empty = lo_full + (NLO > 0 ? NLO : 1);
+    uint64_t *acc_full = lo_empty + (NLO > 0 ? NLO : 1), *acc_empty = acc_full + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -237,8 +241,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&split[s], kEpi);
             mbar_init(&empty[s], 1);
+        }
+        for (int j = 0; j < NLO; ++j) {
+            mbar_init(&lo_full[j], kEpi);
+            mbar_init(&lo_empty[j], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -272,8 +279,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_expect_tx(&full[stage], TX_BYTES);
                 tma_load_2d(A(stage), &tmA, &full[stage], kb * KSTEP_ELEMS, tile * 128);
                 tma_load_2d(B(stage), &tmB, &full[stage], kb * KSTEP_ELEMS, 0);
-                if constexpr (X3)
-                    tma_load_2d(Blo(stage), &tmBlo, &full[stage], kb * KSTEP_ELEMS, 0);
                 if (++stage == STAGES) {
                     stage = 0;
                     phase ^= 1u;
@@ -294,8 +299,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            int stage = 0, buf = 0, pos = 0;
-            uint32_t phase = 0, uses0 = 0, uses1 = 0;
+            int stage = 0, buf = 0, pos = 0, lo = 0;
+            uint32_t phase = 0, lo_phase = 0, uses0 = 0, uses1 = 0;
             for (int64_t it = it0; it < it1; ++it) {
                 const int kb = (int)(it % KB);
                 const bool seg_start = it == it0 || kb == 0;
@@ -314,23 +319,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ++uses0;
                     tc_fence_after();
                 }
-                if (!mbar_wait(X3 ? &split[stage] : &full[stage], phase, deadline, abort_flag))
+                if (!mbar_wait(&full[stage], phase, deadline, abort_flag))
                     break;
+                if constexpr (X3) {
+                    if (!mbar_wait(&lo_full[lo], lo_phase, deadline, abort_flag))
+                        break;
+                }
                 tc_fence_after();
                 const uint32_t d = tmem + buf * BUF_COLS;
                 const uint32_t a0 = su32(A(stage)), b0 = su32(B(stage));
 #pragma unroll
                 for (int kk = 0; kk < KMMA; ++kk) {
                     const uint64_t ad = sdesc(a0 + 32 * kk), bd = sdesc(b0 + 32 * kk);
-                    mma<MODE>(d, ad, bd, ID, (chunk_start && kk == 0) ? 0u : 1u);
+                    // X3: columns [0, NPAD) get A B_hi, columns [NPAD, 2 NPAD) get A B_lo
+                    mma<MODE>(d, ad, bd, ID_B, (chunk_start && kk == 0) ? 0u : 1u);
                     if constexpr (X3) {
-                        const uint64_t adl = sdesc(su32(Alo(stage)) + 32 * kk);
-                        const uint64_t bdl = sdesc(su32(Blo(stage)) + 32 * kk);
-                        mma<MODE>(d, ad, bdl, ID, 1u);
-                        mma<MODE>(d, adl, bd, ID, 1u);
+                        const uint64_t adl = sdesc(su32(LO(lo)) + 32 * kk);
+                        mma<MODE>(d, adl, bd, ID_HI, 1u);   // A_lo x B_hi (first NPAD rows)
                     }
                 }
                 mma_commit(&empty[stage]);
+                if constexpr (X3) {
+                    mma_commit(&lo_empty[lo]);
+                    if (++lo == NLO) {
+                        lo = 0;
+                        lo_phase ^= 1u;
+                    }
+                }
                 if (chunk_end) {
                     mma_commit(&acc_full[buf]);
                     buf ^= 1;
@@ -344,12 +359,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ---------------- split (TF32X3) and accumulation: warps 2..9, 256 threads
         // Thread (quad, lane, half) owns row quad*32 + lane of the tile and
-        // columns [half*HC, half*HC + HC).  Each chunk of DRAIN k blocks is
-        // accumulated by the tensor core in one TMEM buffer, then read here
-        // and added into FP32 registers with round-to-nearest adds: the tensor
-        // core's own accumulation rounds toward zero, which over a long chain
-        // biases the sum low.
-        constexpr int HC = NPAD / 2;                 // columns per thread
+        // columns [half*HC, half*HC + HC) of each accumulator region.  Each
+        // chunk of DRAIN k blocks is accumulated by the tensor core in one
+        // TMEM buffer, then read here and added into FP32 registers with
+        // round-to-nearest adds: the tensor core's own accumulation rounds
+        // toward zero, which over a long chain biases the sum low.
+        // X3 split: the tensor core reads A through its TF32 conversion,
+        // which truncates, so A itself acts as the high part and the
+        // remainder A - trunc(A), rounded to TF32, is written to the low ring.
+        constexpr int HC = NPAD / 2;                 // columns per thread per region
         const int t = threadIdx.x - 64;              // 0..255
         const int quad = warp & 3;                   // TMEM lane quadrant this warp may read
         const int half = (warp - 2) >> 2;
@@ -358,9 +376,27 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < HC; ++j)
             acc[j] = 0.f;
-        int stage = 0, buf = 0, pos = 0, pending = -1;
-        uint32_t phase = 0, drains0 = 0, drains1 = 0;
+        int stage = 0, buf = 0, pos = 0, pending = -1, lo = 0;
+        uint32_t phase = 0, lo_phase = 0, drains0 = 0, drains1 = 0;
         bool ok = true;
+        auto ld_add = [&](uint32_t addr) {
+            if constexpr (HC >= 16) {
+#pragma unroll
+                for (int c0 = 0; c0 < HC; c0 += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(addr + c0, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        acc[c0 + j] += __uint_as_float(v[j]);
+                }
+            } else {
+                uint32_t v[8];
+                tmem_ld8(addr, v);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    acc[j] += __uint_as_float(v[j]);
+            }
+        };
         auto drain = [&](int b) -> bool {
             const uint32_t n = b ? drains1 : drains0;
             if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], n & 1u, deadline, abort_flag)))
@@ -371,22 +407,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ++drains0;
             __syncwarp();
             tc_fence_after();
-            if constexpr (HC >= 16) {
-#pragma unroll
-                for (int c0 = 0; c0 < HC; c0 += 16) {
-                    uint32_t v[16];
-                    tmem_ld16(tmem + b * BUF_COLS + lane_base + c0, v);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        acc[c0 + j] += __uint_as_float(v[j]);
-                }
-            } else {
-                uint32_t v[8];
-                tmem_ld8(tmem + b * BUF_COLS + lane_base, v);
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    acc[j] += __uint_as_float(v[j]);
-            }
+            ld_add(tmem + b * BUF_COLS + lane_base);
+            if constexpr (X3)
+                ld_add(tmem + b * BUF_COLS + NPAD + lane_base);
             tc_fence_before();
             mbar_arrive(&acc_empty[b]);
             return true;
@@ -398,26 +421,31 @@ __global__ void __launch_bounds__(kThreads, 1)
             pos = seg_start ? 0 : pos + 1;
             const bool chunk_end = seg_end || pos % DRAIN == DRAIN - 1;
             if constexpr (X3) {
-                // warp-uniform decision: every lane of the warp continues or none
+                // warp-uniform decisions: every lane of the warp continues or none
                 if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, deadline, abort_flag)))
                     break;
-                float4 *a4 = reinterpret_cast<float4 *>(A(stage));
-                float4 *l4 = reinterpret_cast<float4 *>(Alo(stage));
+                if (!__all_sync(0xffffffffu,
+                                mbar_wait(&lo_empty[lo], lo_phase ^ 1u, deadline, abort_flag)))
+                    break;
+                const float4 *a4 = reinterpret_cast<const float4 *>(A(stage));
+                float4 *l4 = reinterpret_cast<float4 *>(LO(lo));
 #pragma unroll
                 for (int q = 0; q < (int)(kABytes / 16 / kEpi); ++q) {
                     const int idx = t + kEpi * q;
-                    float4 v = a4[idx];
-                    float4 hi;
-                    hi.x = rn_tf32(v.x);
-                    hi.y = rn_tf32(v.y);
-                    hi.z = rn_tf32(v.z);
-                    hi.w = rn_tf32(v.w);
-                    a4[idx] = hi;
-                    l4[idx] = make_float4(rn_tf32(v.x - hi.x), rn_tf32(v.y - hi.y),
-                                          rn_tf32(v.z - hi.z), rn_tf32(v.w - hi.w));
+                    const float4 v = a4[idx];
+                    float4 r;
+                    r.x = rn_tf32(v.x - __uint_as_float(__float_as_uint(v.x) & 0xffffe000u));
+                    r.y = rn_tf32(v.y - __uint_as_float(__float_as_uint(v.y) & 0xffffe000u));
+                    r.z = rn_tf32(v.z - __uint_as_float(__float_as_uint(v.z) & 0xffffe000u));
+                    r.w = rn_tf32(v.w - __uint_as_float(__float_as_uint(v.w) & 0xffffe000u));
+                    l4[idx] = r;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(&split[stage]);
+                mbar_arrive(&lo_full[lo]);
+                if (++lo == NLO) {
+                    lo = 0;
+                    lo_phase ^= 1u;
+                }
             }
             if (++stage == STAGES) {
                 stage = 0;
@@ -479,12 +507,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---- factor packing: X (K x r, row-major) -> B (NPAD x Kp, K contiguous) --
-// mode TF32: raw FP32; TF32X3: high part (TF32-exact) and remainder; BF16:
-// round to nearest BF16.  Rows r..NPAD-1 and columns K..Kp-1 are zero.
+// mode TF32: raw FP32; TF32X3: 2 NPAD rows, the TF32 high part stacked over
+// the TF32 remainder; BF16: round to nearest BF16.  Rows r..NPAD-1 (of each
+// part) and columns K..Kp-1 are zero.
 template <int MODE>
 __global__ void k_pack_factor(const float *__restrict__ X, int64_t K, int r, int npad, int64_t kp,
                               void *__restrict__ Bhi, float *__restrict__ Blo)
 {
+    // TF32X3: Bhi rows [0, npad) hold the nearest TF32 value, Blo (= rows
+    // [npad, 2 npad) of the same buffer) the nearest TF32 value of the rest
     __shared__ float t[32][33];
     const int64_t k0 = (int64_t)blockIdx.x * 32;
     const int n0 = blockIdx.y * 32;
@@ -548,44 +579,44 @@ bool make_map(CUtensorMap *m, const void *base, bool bf16, uint64_t inner, uint6
 }
 
 template <int MODE, int NPAD>
-constexpr int stages_for()
-{
-    constexpr int stage = (MODE == TC_TF32X3 ? 2 : 1) * (kABytes + NPAD * 128);
-    constexpr int s = (200 * 1024) / stage;
-    return s > 8 ? 8 : s;
-}
+struct TcCfg {
+    static constexpr int NLO = MODE == TC_TF32X3 ? 2 : 0;       // low-part ring
+    static constexpr int NB = MODE == TC_TF32X3 ? 2 * NPAD : NPAD;
+    static constexpr int STAGE = kABytes + NB * 128;
+    static constexpr int ST0 = (200 * 1024 - NLO * (int)kABytes) / STAGE;
+    static constexpr int STAGES = ST0 > 8 ? 8 : ST0;
+    static constexpr int DRAIN = MODE == TC_TF32X3 ? 1 : 2;     // k blocks per chunk
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE + (size_t)NLO * kABytes + 1024 + 256;
+};
 
 template <int MODE, int NPAD>
-cudaError_t launch_mode(const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &bl,
-                        const TcArgs &p, cudaStream_t s)
+cudaError_t launch_mode(const CUtensorMap &a, const CUtensorMap &b, const TcArgs &p,
+                        cudaStream_t s)
 {
-    constexpr int ST = stages_for<MODE, NPAD>();
-    constexpr int stage = (MODE == TC_TF32X3 ? 2 : 1) * (kABytes + NPAD * 128);
-    const size_t smem = (size_t)ST * stage + 1024 + 256;
-    constexpr int DR = MODE == TC_TF32X3 ? 1 : 2;   // k blocks per accumulator chunk
+    using C = TcCfg<MODE, NPAD>;
+    auto kern = k_tc_cross<MODE, NPAD, C::STAGES, C::NLO, C::DRAIN>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_cross<MODE, NPAD, ST, DR>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::SMEM);
         if (e != cudaSuccess)
             return e;
         attr = true;
     }
-    k_tc_cross<MODE, NPAD, ST, DR><<<p.grid, kThreads, smem, s>>>(a, b, bl, p);
+    kern<<<p.grid, kThreads, C::SMEM, s>>>(a, b, p);
     count_launch();
     return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t launch_npad(int npad, const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &bl,
-                        const TcArgs &p, cudaStream_t s)
+cudaError_t launch_npad(int npad, const CUtensorMap &a, const CUtensorMap &b, const TcArgs &p,
+                        cudaStream_t s)
 {
     switch (npad) {
-    case 16: return launch_mode<MODE, 16>(a, b, bl, p, s);
-    case 32: return launch_mode<MODE, 32>(a, b, bl, p, s);
-    case 64: return launch_mode<MODE, 64>(a, b, bl, p, s);
-    default: return launch_mode<MODE, 128>(a, b, bl, p, s);
+    case 16: return launch_mode<MODE, 16>(a, b, p, s);
+    case 32: return launch_mode<MODE, 32>(a, b, p, s);
+    case 64: return launch_mode<MODE, 64>(a, b, p, s);
+    default: return launch_mode<MODE, 128>(a, b, p, s);
     }
 }
 
@@ -612,7 +643,7 @@ size_t tc_pack_bytes(int64_t K, int r, int mode)
 {
     const int64_t kp = tc_kpad(K, mode);
     const size_t e = mode == TC_BF16 ? 2 : 4;
-    return (size_t)tc_npad(r) * kp * e * (mode == TC_TF32X3 ? 2 : 1) + 512;
+    return (size_t)tc_npad(r) * kp * e * (mode == TC_TF32X3 ? 2 : 1) + 256;
 }
 
 cudaError_t launch_tc_pack(const float *X, int64_t K, int r, int mode, void *pack, cudaStream_t s)
@@ -621,7 +652,7 @@ cudaError_t launch_tc_pack(const float *X, int64_t K, int r, int mode, void *pac
     const int npad = tc_npad(r);
     const int64_t kp = tc_kpad(K, mode);
     const size_t hb = (size_t)npad * kp * (mode == TC_BF16 ? 2 : 4);
-    float *lo = reinterpret_cast<float *>(reinterpret_cast<char *>(pack) + ((hb + 255) & ~size_t(255)));
+    float *lo = reinterpret_cast<float *>(reinterpret_cast<char *>(pack) + hb);   // rows npad..
     dim3 grid((unsigned)((kp + 31) / 32), (unsigned)((npad + 31) / 32));
     dim3 blk(32, 8);
     if (mode == TC_BF16)
@@ -672,21 +703,12 @@ cudaError_t launch_tc_cross(const void *A, int64_t M, int64_t K, int64_t lda, in
     const bool bf = mode == TC_BF16;
     const int64_t kp = tc_kpad(K, mode);
     const size_t es = bf ? 2 : 4;
-    const size_t hb = (size_t)npad * kp * es;
-    const void *lo = reinterpret_cast<const char *>(pack) + ((hb + 255) & ~size_t(255));
-    CUtensorMap ma, mb, ml;
+    const uint32_t nb = mode == TC_TF32X3 ? 2 * npad : npad;   // packed rows ([hi; lo] for X3)
+    CUtensorMap ma, mb;
     const uint32_t box_k = bf ? 64 : 32;
     if (!make_map(&ma, A, bf, (uint64_t)K, (uint64_t)M, (uint64_t)lda * es, box_k, 128) ||
-        !make_map(&mb, pack, bf, (uint64_t)kp, (uint64_t)npad, (uint64_t)kp * es, box_k,
-                  (uint32_t)npad))
+        !make_map(&mb, pack, bf, (uint64_t)kp, (uint64_t)nb, (uint64_t)kp * es, box_k, nb))
         return cudaErrorInvalidValue;
-    if (mode == TC_TF32X3) {
-        if (!make_map(&ml, lo, false, (uint64_t)kp, (uint64_t)npad, (uint64_t)kp * 4, box_k,
-                      (uint32_t)npad))
-            return cudaErrorInvalidValue;
-    } else {
-        ml = mb;
-    }
     TcArgs p{};
     p.M = M;
     p.r = r;
@@ -697,10 +719,10 @@ cudaError_t launch_tc_cross(const void *A, int64_t M, int64_t K, int64_t lda, in
     p.P = P;
     p.status = status;
     if (mode == TC_BF16)
-        return launch_npad<TC_BF16>(npad, ma, mb, ml, p, s);
+        return launch_npad<TC_BF16>(npad, ma, mb, p, s);
     if (mode == TC_TF32X3)
-        return launch_npad<TC_TF32X3>(npad, ma, mb, ml, p, s);
-    return launch_npad<TC_TF32>(npad, ma, mb, ml, p, s);
+        return launch_npad<TC_TF32X3>(npad, ma, mb, p, s);
+    return launch_npad<TC_TF32>(npad, ma, mb, p, s);
 }
 
 }  // namespace nmfi
