@@ -191,6 +191,107 @@ def reference_arm(args, rank, world):
     }))
 
 
+# ---------------------------------------------------------------- serving
+SERVE_ROWS, SERVE_R, SERVE_RATE = 50000, 128, 2000.0
+BATCH_COUNT = 256
+
+
+def serve_measurement(P, torch, dev, seed, seconds=3.0, pool=64):
+    """Continuous-batching projection onto a fixed 50000 x 128 basis (U[0,1],
+    unit-norm columns): Poisson arrivals at 2000 requests/s, widths
+    log-uniform on [1, 4096] new columns of 100 Zipf-popular nonzeros each.
+    Request contents cycle through a pool of generated blocks; arrival times
+    and order are fresh.  Latency = submit -> result in host memory."""
+    import numpy as np
+
+    import workloads as WL
+    wl = WL.serving(seed=seed, rows=SERVE_ROWS, r=SERVE_R, rate=SERVE_RATE, duration=seconds,
+                    max_requests=pool)
+    g = WL.rng(seed + 1)
+    n = int(g.poisson(SERVE_RATE * seconds))
+    arrivals = np.cumsum(g.exponential(1.0 / SERVE_RATE, size=n))
+    pick = g.integers(0, len(wl.requests), size=n)
+    W = torch.tensor(wl.W, device=dev)
+    srv = P.Server(W, slots=8, max_batch_cols=16384, max_batch_nnz=1 << 21, hbm_budget=2 << 30,
+                   nnls=P.nnls_opts(max_inner=50, eps=1e-3))
+    # warm-up: one of each pool entry
+    for rq in wl.requests[:8]:
+        t, _ = srv.submit(*rq)
+        srv.wait(t)
+    tickets = []
+    t0 = time.perf_counter()
+    for a, k in zip(arrivals, pick):
+        now = time.perf_counter() - t0
+        if a > now:
+            time.sleep(a - now)
+        tickets.append(srv.submit(*wl.requests[k])[0])
+    lat = np.array([srv.wait(t) for t in tickets])
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    cols = sum(len(wl.requests[k][0]) - 1 for k in pick)
+    return {"workload": "serve50000x128", "requests": n, "offered_req_s": SERVE_RATE,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "cols_per_s": cols / wall, "req_per_s": n / wall,
+            "batches": st["batches"], "max_queue": st["max_queue"], "slots": 8,
+            "note": "latency = submit to result in host memory, through nmf_server_*"}
+
+
+def batched_measurement(P, torch, dev, h, seed, iters=20, warmup=3):
+    """256 independent dense instances, m ~ U[100,4000], n ~ U[100,2000],
+    r in {8,16,32,64}, V = W0 H0 + |N(0,0.01)| with U[0,1] factors (FP32).
+    Each launch shape runs `iters` outer iterations from the same start after
+    `warmup` untimed ones: the persistent launch in a CUDA graph, the same with
+    the autotuned shape, and the per-instance launch loop.  Device time comes
+    from CUDA events inside nmf_solve_batched."""
+    import numpy as np
+
+    import workloads as WL
+    insts = WL.batched(seed=seed, count=BATCH_COUNT, workers=max(1, os.cpu_count() or 1))
+    dv, init = [], []
+    for inst in insts:
+        V = torch.from_numpy(inst.V).to(dev)
+        W = torch.from_numpy(inst.W0).to(dev)
+        Ht = torch.from_numpy(inst.Ht0).to(dev)
+        dv.append((V, V.t().contiguous(), W, Ht))
+        init.append((W.clone(), Ht.clone()))
+    del insts
+
+    def reset():
+        for (_, _, W, Ht), (W0, H0) in zip(dv, init):
+            W.copy_(W0)
+            Ht.copy_(H0)
+
+    nn = P.nnls_opts(max_inner=50, eps=1e-3)
+    res = {}
+    for mode in ("persistent", "autotune", "loop"):
+        reset()
+        P.nmf_solve_batched(h, dv, P.solve_opts(warmup, nnls=nn, use_graph=True), mode="persistent")
+        reset()
+        l0 = P.launch_count()
+        reps = P.nmf_solve_batched(h, dv, P.solve_opts(iters, nnls=nn, use_graph=True), mode=mode)
+        res[mode] = {"ms_per_iter": reps[0].ms_total / iters, "launches": P.launch_count() - l0,
+                     "kbar": reps[0].kbar,
+                     "J_mean": float(np.mean([rp.objective for rp in reps]))}
+    # algorithmic FP32 work of one outer iteration (both half-steps)
+    flops = 0.0
+    vbytes = 0.0
+    for (V, _, W, _) in dv:
+        m, n = V.shape
+        r = W.shape[1]
+        flops += 2.0 * 2.0 * m * n * r + 2.0 * r * r * (m + n)
+        vbytes += 8.0 * m * n
+    del dv, init
+    torch.cuda.empty_cache()
+    pm = res["persistent"]["ms_per_iter"]
+    return {"workload": f"batched{BATCH_COUNT}_m100-4000_n100-2000_r8-64", "iters": iters,
+            "modes": res, "speedup_persistent_vs_loop": res["loop"]["ms_per_iter"] / pm,
+            "gemm_tflops_persistent": flops / (pm * 1e-3) / 1e12,
+            "v_read_gbs_persistent": vbytes / (pm * 1e-3) / 1e9,
+            "note": "FP32 on CUDA cores; ms_per_iter = device time / iterations (autotune "
+                    "includes its timed candidate iterations)"}
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -200,6 +301,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16", "fp32_simt"],
+                    help="cross-term arithmetic of --profile runs")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the many-instance measurement")
+    ap.add_argument("--batched-iters", type=int, default=20)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the TF32 / BF16 time-to-gap variants")
     ap.add_argument("--profile", action="store_true",
                     help="for ncu: 300 warm outer iterations, then 10 inside NVTX range "
                          "'profiled'; prints per-kernel-class times and exits")
@@ -240,23 +350,23 @@ def main():
     Ht = H0.clone()
     h = P.Handle(local_rank)
 
-    def opts(iters, eps, hist=None, target=0.0, fstar=0.0, check=CHECK_EVERY):
+    def opts(iters, eps, hist=None, target=0.0, fstar=0.0, check=CHECK_EVERY, prec="fp32"):
         hp = hist.ctypes.data_as(C.POINTER(C.c_double)) if hist is not None else None
         return P.solve_opts(iters, rel_gap_target=target, f_star=fstar, beta_w=inst.beta_w,
                             beta_h=inst.beta_h, nnls=P.nnls_opts(max_inner=50, eps=eps),
-                            objective="direct", obj_hist=hp, check_every=check)
+                            objective="direct", obj_hist=hp, check_every=check, prec=prec)
 
     if args.profile:
         W.copy_(W0)
         Ht.copy_(H0)
-        P.nmf_solve(h, V, W, Ht, opts(300, 1e-3, check=0), Vt=Vt)
+        P.nmf_solve(h, V, W, Ht, opts(300, 1e-3, check=0, prec=args.prec), Vt=Vt)
         torch.cuda.synchronize()
         P.nmf_profile_enable(True)
         torch.cuda.nvtx.range_push("profiled")
-        rp = P.nmf_solve(h, V, W, Ht, opts(10, 1e-3, check=0), Vt=Vt)
+        rp = P.nmf_solve(h, V, W, Ht, opts(10, 1e-3, check=0, prec=args.prec), Vt=Vt)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        print(json.dumps({"profile": WORKLOAD, "iters": 10, "kbar": rp.kbar,
+        print(json.dumps({"profile": WORKLOAD, "prec": args.prec, "iters": 10, "kbar": rp.kbar,
                           "kernels": {k: P.nmf_profile_read(k) for k in P.KCLASS}}))
         P.nmf_profile_enable(False)
         return
@@ -310,6 +420,29 @@ def main():
     reached = all(rp.rel_gap <= GAP for rp in reps)
     inner = sum(rp.inner_total for rp in reps)
 
+    # ---- precision variants: the same time-to-gap measurement with TF32 and
+    # BF16 cross terms (one warm-up and one timed solve each; same J*)
+    variants = {}
+    if not args.no_variants:
+        for vp in ("tf32", "bf16"):
+            vo = opts(8 * T_CONF, 1e-3, target=GAP, fstar=jstar, prec=vp)
+
+            def vstep():
+                W.copy_(W0)
+                Ht.copy_(H0)
+                return P.nmf_solve(h, V, W, Ht, vo, Vt=Vt)
+
+            vstep()
+            torch.cuda.synchronize()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record()
+            vr = vstep()
+            v1.record()
+            torch.cuda.synchronize()
+            variants[vp] = {"ms_to_gap": v0.elapsed_time(v1), "iters": vr.iters_done,
+                            "reached": vr.rel_gap <= GAP, "final_gap": vr.rel_gap}
+
     # ---- end to end through the C ABI with host buffers (pinned)
     Vh = torch.tensor(inst.V).pin_memory()
     W0h = torch.tensor(inst.W0).pin_memory()
@@ -332,6 +465,10 @@ def main():
     h2d = Vh.numel() * 4 + W0h.numel() * 4 + H0h.numel() * 4
     d2h = Wh.numel() * 4 + Hh.numel() * 4 + 8
 
+    serve = None if args.no_serve else serve_measurement(P, torch, dev, args.seed,
+                                                             seconds=args.serve_seconds)
+    batched = None if args.no_batched else batched_measurement(P, torch, dev, h, args.seed,
+                                                               iters=args.batched_iters)
     if rank != 0:
         return
     peaks, peak_src = load_peaks()
@@ -408,6 +545,9 @@ def main():
                    "l2": "inputs larger than L2 (V and V^T are 164 MB each)"},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "variants": variants,
+        "serve": serve,
+        "batched": batched,
         "gpu_launches": launches,
         "roofline": roof,
         "kernels": per_class,

@@ -232,6 +232,36 @@ nmf_status nmf_kkt(nmf_handle h, const float *Q, const float *C, int64_t rows, i
 nmf_status nmf_solve(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt, int r, float *W,
                      float *Ht, const nmf_solve_opts *opts, nmf_report *rep);
 
+/* ---- many independent instances ------------------------------------------ */
+
+/* One NMF instance of a batch (all pointers device memory, row-major F32,
+ * contiguous): V m x n and its transpose Vt n x m, W m x r, Ht n x r (initial
+ * factors in, result out).  r <= 64. */
+typedef struct {
+    int64_t m, n;
+    int r;
+    const float *V, *Vt;
+    float *W, *Ht;
+} nmf_instance;
+
+/* Advance `count` independent instances by opts->outer_iters outer
+ * iterations of Alg. 2 each (shared L1/L2 weights and NNLS options; FP32 on
+ * CUDA cores).
+ *  mode 0: persistent - one cooperative launch per outer iteration runs all
+ *          eight phases (Gram, rescale, cross term, NNLS for W, then for H)
+ *          for all instances with grid barriers between phases; captured in
+ *          a CUDA graph when opts->use_graph;
+ *  mode 1: per-instance loop - the same phase code launched per instance and
+ *          phase (the baseline);
+ *  mode 2: as mode 0, with the first iterations spent timing candidate
+ *          launch shapes (CTAs per SM, NNLS rows per work item) and the
+ *          fastest kept for the rest.
+ * reps (host, `count` entries, optional) receive each instance's final J
+ * (FP64 element-wise objective), iterations and, in every entry, the batch's
+ * device time and mean inner iterations.  Synchronises before returning. */
+nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance *inst,
+                             const nmf_solve_opts *opts, int mode, nmf_report *reps);
+
 /* ---- projection onto a fixed basis ----------------------------------------- */
 
 /* E-step alone (Alg. 1 E-step, Alg. 2 first loop) against a fixed basis W
@@ -242,6 +272,56 @@ nmf_status nmf_solve(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt, in
 nmf_status nmf_project(nmf_handle h, const float *Qt, const float *d, const float *W,
                        int64_t wrows, int r, const nmf_csr *VnewT, float *Hnew,
                        const nmf_nnls_opts *opts);
+
+/* ---- projection server: continuous batching -------------------------------- */
+
+/* A server projects incoming blocks of new data columns onto a fixed basis W
+ * (the E-step alone, as nmf_project), batching requests continuously: a
+ * scheduler thread admits queued requests, in arrival order, into the next
+ * free slot while the batch fits the slot and the bytes of all batches in
+ * flight stay within hbm_budget; each slot runs its batch (host-to-device
+ * copy, SpMM, NNLS, device-to-host copy) on its own CUDA stream, so batches
+ * overlap.  A result depends on its own columns only: it is bitwise the same
+ * alone and inside any mix of requests. */
+typedef struct nmf_server_s *nmf_server_t;
+
+typedef struct {
+    int slots;               /* batches in flight, one CUDA stream each (1..64)  */
+    int64_t max_batch_cols;  /* new columns per batch (a slot's capacity)        */
+    int64_t max_batch_nnz;   /* nonzeros per batch                               */
+    size_t hbm_budget;       /* device bytes all batches in flight may hold      */
+    nmf_nnls_opts nnls;      /* NNLS options (zeroed: defaults)                   */
+} nmf_server_opts_t;
+
+typedef struct {
+    int64_t completed;       /* requests finished                                 */
+    int64_t completed_cols;  /* new columns finished                              */
+    int64_t batches;         /* batches launched                                  */
+    int64_t queued;          /* requests waiting for admission now                */
+    int64_t max_queue;       /* largest queue seen                                */
+    int64_t inflight_bytes;  /* device bytes held by batches in flight now       */
+} nmf_server_stats_t;
+
+/* Create a server for basis W (device memory, wrows x r, F32, kept alive by
+ * the caller until nmf_server_destroy).  Allocates the slots' device and
+ * pinned host buffers and computes the basis' rescaled Gram once. */
+nmf_status nmf_server_create(nmf_server_t *out, int device, const float *W, int64_t wrows, int r,
+                             const nmf_server_opts_t *opts);
+/* Queue a request: w new columns as HOST CSR over the basis rows (rowptr
+ * w + 1 entries, colidx/vals nnz entries, copied before returning); `out`
+ * (HOST, w x r F32) receives the nonnegative coefficients when the ticket
+ * completes.  NMF_E_BUSY if the request exceeds a slot or the budget (it
+ * could never be admitted); NMF_E_ARG on malformed CSR. */
+nmf_status nmf_server_submit(nmf_server_t s, int64_t w, int64_t nnz, const int64_t *rowptr,
+                             const int32_t *colidx, const float *vals, float *out,
+                             int64_t *ticket);
+/* Wait for a ticket (at most timeout_s seconds: NMF_E_TIMEOUT); latency_ms
+ * (optional) receives submit-to-result time. */
+nmf_status nmf_server_wait(nmf_server_t s, int64_t ticket, double timeout_s, double *latency_ms);
+/* Counters; returns a latched error of the scheduler, if any. */
+nmf_status nmf_server_stats(nmf_server_t s, nmf_server_stats_t *st);
+/* Finish queued work, then free everything the server holds. */
+nmf_status nmf_server_destroy(nmf_server_t s);
 
 /* ---- allocation-free variant ----------------------------------------------- */
 

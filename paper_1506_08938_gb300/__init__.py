@@ -65,6 +65,21 @@ class Report(C.Structure):
                 ("inner_total", C.c_int64)]
 
 
+class Instance(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("r", C.c_int), ("V", C.c_void_p),
+                ("Vt", C.c_void_p), ("W", C.c_void_p), ("Ht", C.c_void_p)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("slots", C.c_int), ("max_batch_cols", C.c_int64), ("max_batch_nnz", C.c_int64),
+                ("hbm_budget", C.c_size_t), ("nnls", NnlsOpts)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("completed_cols", C.c_int64), ("batches", C.c_int64),
+                ("queued", C.c_int64), ("max_queue", C.c_int64), ("inflight_bytes", C.c_int64)]
+
+
 _lib = None
 _lock = threading.Lock()
 _P = C.c_void_p
@@ -96,9 +111,18 @@ def _load():
                                        C.c_float, C.c_float, C.c_float, _P]
     L.nmf_solve.argtypes = [_P, C.POINTER(Matrix), C.POINTER(Matrix), C.c_int, _P, _P,
                             C.POINTER(SolveOpts), C.POINTER(Report)]
+    L.nmf_solve_batched.argtypes = [_P, C.c_int, C.POINTER(Instance), C.POINTER(SolveOpts),
+                                    C.c_int, C.POINTER(Report)]
     L.nmf_project.argtypes = [_P, _P, _P, _P, C.c_int64, C.c_int, C.POINTER(Csr), _P,
                               C.POINTER(NnlsOpts)]
     L.nmf_gram_noalloc.argtypes = [C.POINTER(Dense), C.c_float, _P, _P]
+    L.nmf_server_create.argtypes = [C.POINTER(_P), C.c_int, _P, C.c_int64, C.c_int,
+                                    C.POINTER(ServerOpts)]
+    L.nmf_server_submit.argtypes = [_P, C.c_int64, C.c_int64, _P, _P, _P, _P,
+                                    C.POINTER(C.c_int64)]
+    L.nmf_server_wait.argtypes = [_P, C.c_int64, C.c_double, C.POINTER(C.c_double)]
+    L.nmf_server_stats.argtypes = [_P, C.POINTER(ServerStats)]
+    L.nmf_server_destroy.argtypes = [_P]
     L.nmf_profile_enable.argtypes = [C.c_int]
     L.nmf_profile_read.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     return L
@@ -361,6 +385,32 @@ def nmf_solve(h: Handle, V, W, Ht, opts: SolveOpts, Vt=None, csr_parts=None, csr
     return rep
 
 
+_BATCH_MODES = {"persistent": 0, "loop": 1, "autotune": 2}
+
+
+def nmf_solve_batched(h: Handle, instances, opts: SolveOpts, mode="persistent"):
+    """Advance independent instances, each a tuple (V, Vt, W, Ht) of device
+    tensors (V m x n, Vt its n x m transpose, W m x r, Ht n x r, r <= 64), by
+    opts.outer_iters outer iterations, in place.  mode: "persistent" (one
+    cooperative launch per iteration for all instances), "loop" (launches per
+    instance and phase) or "autotune".  Returns one Report per instance."""
+    arr = (Instance * len(instances))()
+    for k, (V, Vt, W, Ht) in enumerate(instances):
+        _need_cuda(V, Vt, W, Ht)
+        m, n = V.shape
+        r = W.shape[1]
+        if Vt.shape != (n, m) or W.shape != (m, r) or Ht.shape != (n, r):
+            raise ValueError(f"instance {k}: inconsistent shapes")
+        for t in (V, Vt, W, Ht):
+            if _dt(t) != NMF_F32 or not t.is_contiguous():
+                raise ValueError(f"instance {k}: tensors must be contiguous float32")
+        arr[k] = Instance(m, n, r, _ptr(V), _ptr(Vt), _ptr(W), _ptr(Ht))
+    reps = (Report * len(instances))()
+    _check(lib().nmf_solve_batched(h.h, len(instances), arr, C.byref(opts),
+                                   _BATCH_MODES[mode], reps), "nmf_solve_batched")
+    return list(reps)
+
+
 def nmf_project(h: Handle, Qt, d, W, csr_parts, Hnew, opts: NnlsOpts | None = None):
     rp, ci, va, ncols = csr_parts
     _need_cuda(Qt, d, W, rp, ci, va, Hnew)
@@ -369,3 +419,62 @@ def nmf_project(h: Handle, Qt, d, W, csr_parts, Hnew, opts: NnlsOpts | None = No
                              C.byref(cs), _ptr(Hnew), C.byref(opts) if opts else None),
            "nmf_project")
     return Hnew
+
+
+class Server:
+    """nmf_server_*: continuous-batching projection onto a fixed basis W
+    (device tensor, kept referenced here).  Requests are host CSR blocks
+    (numpy int64 rowptr, int32 colidx, float32 vals); results land in host
+    numpy arrays."""
+
+    def __init__(self, W, slots=4, max_batch_cols=8192, max_batch_nnz=1 << 20,
+                 hbm_budget=1 << 30, nnls: NnlsOpts | None = None, device=0):
+        _need_cuda(W)
+        self._W = W
+        o = ServerOpts(int(slots), int(max_batch_cols), int(max_batch_nnz), int(hbm_budget),
+                       nnls or nnls_opts())
+        s = C.c_void_p()
+        _check(lib().nmf_server_create(C.byref(s), int(device), _ptr(W), W.shape[0], W.shape[1],
+                                       C.byref(o)), "nmf_server_create")
+        self.s = s
+        self.r = W.shape[1]
+        self._keep = {}
+
+    def submit(self, rowptr, colidx, vals, out=None):
+        import numpy as np
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float32)
+        w = len(rowptr) - 1
+        out = out if out is not None else np.zeros((w, self.r), dtype=np.float32)
+        t = C.c_int64()
+        _check(lib().nmf_server_submit(self.s, w, len(vals), rowptr.ctypes.data_as(C.c_void_p),
+                                       colidx.ctypes.data_as(C.c_void_p),
+                                       vals.ctypes.data_as(C.c_void_p),
+                                       out.ctypes.data_as(C.c_void_p), C.byref(t)),
+               "nmf_server_submit")
+        self._keep[t.value] = out
+        return t.value, out
+
+    def wait(self, ticket, timeout=60.0):
+        lat = C.c_double()
+        _check(lib().nmf_server_wait(self.s, int(ticket), float(timeout), C.byref(lat)),
+               "nmf_server_wait")
+        self._keep.pop(ticket, None)
+        return lat.value
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().nmf_server_stats(self.s, C.byref(st)), "nmf_server_stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().nmf_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -57,12 +57,15 @@ struct Prof {
 Prof g_prof;
 }  // namespace
 
+thread_local bool tl_prof_off = false;
+
 void prof_suspend(bool on) { g_prof.suspended += on ? 1 : -1; }
+void prof_thread_off() { tl_prof_off = true; }
 
 void prof_mark(int cls, cudaStream_t s, bool begin)
 {
     Prof &P = g_prof;
-    if (!P.on || P.suspended > 0)
+    if (!P.on || P.suspended > 0 || tl_prof_off)
         return;
     if (begin) {
         if (P.used + 2 > 4096)
@@ -1214,6 +1217,256 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// many independent instances
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchPlan {
+    BatchInst *dinst = nullptr;   // device array
+    int64_t *doff = nullptr;      // device [8][count + 1]
+    std::vector<int64_t> hoff;    // host copy
+};
+
+nmf_status batch_offsets(std::vector<int64_t> &hoff, const nmf_instance *inst, int count,
+                         int nnls_rows)
+{
+    hoff.assign((size_t)8 * (count + 1), 0);
+    for (int ph = 0; ph < 8; ++ph) {
+        int64_t acc = 0;
+        for (int i = 0; i < count; ++i) {
+            hoff[(size_t)ph * (count + 1) + i] = acc;
+            acc += batched_items(ph, inst[i].m, inst[i].n, nnls_rows);
+        }
+        hoff[(size_t)ph * (count + 1) + count] = acc;
+    }
+    return NMF_OK;
+}
+
+}  // namespace
+
+NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance *inst,
+                                     const nmf_solve_opts *opts, int mode, nmf_report *reps)
+{
+    if (!h || !inst || !opts || count < 1 || mode < 0 || mode > 2)
+        return NMF_E_ARG;
+    if (opts->outer_iters < 0)
+        return NMF_E_ARG;
+    for (int i = 0; i < count; ++i) {
+        const nmf_instance &b = inst[i];
+        if (b.m < 1 || b.n < 1 || b.r < 1 || b.r > 64)
+            return NMF_E_SHAPE;
+        if (!b.V || !b.Vt || !b.W || !b.Ht)
+            return NMF_E_ARG;
+    }
+    CK(cudaSetDevice(h->device));
+    const nmf_nnls_opts nn = opts_or_default(&opts->nnls);
+    // ---- workspace: per-instance buffers, then the device tables
+    Sizer z;
+    for (int i = 0; i < count; ++i) {
+        const nmf_instance &b = inst[i];
+        const int64_t parts = (std::max(b.m, b.n) + 255) / 256;
+        z.add<float>((size_t)parts * b.r * b.r);
+        z.add<float>((size_t)b.r * b.r);
+        z.add<float>(b.r);
+        z.add<float>((size_t)b.m * b.r);
+        z.add<float>((size_t)b.n * b.r);
+    }
+    z.add<BatchInst>(count);
+    z.add<int64_t>((size_t)8 * (count + 1));
+    nmf_status st = ensure_ws(h, z.off);
+    if (st)
+        return st;
+    Arena a(h->ws, h->ws_cap);
+    std::vector<BatchInst> hb(count);
+    for (int i = 0; i < count; ++i) {
+        const nmf_instance &b = inst[i];
+        BatchInst &q = hb[i];
+        q.m = b.m;
+        q.n = b.n;
+        q.r = b.r;
+        q.V = b.V;
+        q.Vt = b.Vt;
+        q.W = b.W;
+        q.Ht = b.Ht;
+        const int64_t parts = (std::max(b.m, b.n) + 255) / 256;
+        q.gram = a.take<float>((size_t)parts * b.r * b.r);
+        q.Qt = a.take<float>((size_t)b.r * b.r);
+        q.d = a.take<float>(b.r);
+        q.Cw = a.take<float>((size_t)b.m * b.r);
+        q.Ch = a.take<float>((size_t)b.n * b.r);
+        q.alpha_w = opts->alpha_w;
+        q.alpha_h = opts->alpha_h;
+        q.beta_w = opts->beta_w;
+        q.beta_h = opts->beta_h;
+    }
+    BatchInst *dinst = a.take<BatchInst>(count);
+    int64_t *doff = a.take<int64_t>((size_t)8 * (count + 1));
+    cudaStream_t s = h->stream;
+    CK(cudaMemcpyAsync(dinst, hb.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, s));
+
+    BatchArgs ba{};
+    ba.inst = dinst;
+    ba.count = count;
+    ba.item_off = doff;
+    ba.nnls.max_inner = nn.max_inner;
+    ba.nnls.eps = (float)nn.eps;
+    ba.nnls.cd_steps = nn.cd_steps;
+    ba.iter_total = h->ctr + 1;
+    ba.status = h->status;
+    ba.bar_count = reinterpret_cast<unsigned *>(h->idev + 2);
+    ba.bar_gen = reinterpret_cast<unsigned *>(h->idev + 3);
+    CK(cudaMemsetAsync(h->ctr + 1, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(h->idev + 2, 0, 2 * sizeof(int), s));
+
+    std::vector<int64_t> hoff;
+    auto set_rows = [&](int rows) -> nmf_status {
+        ba.nnls_rows = rows;
+        batch_offsets(hoff, inst, count, rows);
+        CK(cudaMemcpyAsync(doff, hoff.data(), sizeof(int64_t) * hoff.size(),
+                           cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));   // hoff is reused
+        return NMF_OK;
+    };
+    if ((st = set_rows(32)))
+        return st;
+    const int max_grid = batched_grid(true);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = max_grid;
+
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int t = 0;
+    auto one_persistent = [&]() -> nmf_status {
+        ba.phase_begin = 0;   // all eight phases, all instances
+        ba.phase_end = 8;
+        ba.inst_begin = -1;
+        CK(launch_batched(ba, grid, true, s));
+        return NMF_OK;
+    };
+    CK(cudaEventRecord(e0, s));
+    if (mode == 2) {
+        // autotune: each candidate runs one real outer iteration, timed
+        const int per_sm_max = std::max(1, max_grid / sms);
+        float best = 1e30f;
+        int best_grid = max_grid, best_rows = 32;
+        const int rows_c[3] = {16, 32, 64};
+        for (int ri = 0; ri < 3 && t < opts->outer_iters; ++ri) {
+            if ((st = set_rows(rows_c[ri])))
+                return st;
+            for (int k = 1; k <= per_sm_max && t < opts->outer_iters; ++k) {
+                grid = k * sms;
+                cudaEvent_t a0, a1;
+                CK(cudaEventCreate(&a0));
+                CK(cudaEventCreate(&a1));
+                CK(cudaEventRecord(a0, s));
+                if ((st = one_persistent()))
+                    return st;
+                CK(cudaEventRecord(a1, s));
+                CK(cudaEventSynchronize(a1));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a0, a1);
+                cudaEventDestroy(a0);
+                cudaEventDestroy(a1);
+                ++t;
+                if (ms < best) {
+                    best = ms;
+                    best_grid = grid;
+                    best_rows = rows_c[ri];
+                }
+            }
+        }
+        grid = best_grid;
+        if ((st = set_rows(best_rows)))
+            return st;
+    }
+    if (mode == 0 || mode == 2) {
+        ba.phase_begin = 0;
+        ba.phase_end = 8;
+        ba.inst_begin = -1;
+        cudaGraphExec_t gexec = nullptr;
+        if (opts->use_graph && t < opts->outer_iters) {
+            if (!h->cap)
+                CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+            CK(cudaStreamSynchronize(s));
+            prof_suspend(true);
+            cudaGraph_t g = nullptr;
+            bool ok = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) ==
+                      cudaSuccess;
+            if (ok) {
+                ok = launch_batched(ba, grid, true, h->cap) == cudaSuccess;
+                ok = (cudaStreamEndCapture(h->cap, &g) == cudaSuccess) && ok;
+            }
+            prof_suspend(false);
+            if (ok && g && cudaGraphInstantiate(&gexec, g, 0) == cudaSuccess) {
+                g_launches.fetch_sub(1);
+            } else {
+                gexec = nullptr;   // capture of a cooperative launch refused: launch directly
+                cudaGetLastError();
+            }
+            if (g)
+                cudaGraphDestroy(g);
+        }
+        for (; t < opts->outer_iters; ++t) {
+            if (gexec) {
+                CK(cudaGraphLaunch(gexec, s));
+                count_launch();
+            } else if ((st = one_persistent())) {
+                return st;
+            }
+        }
+        if (gexec)
+            cudaGraphExecDestroy(gexec);
+    } else {
+        for (; t < opts->outer_iters; ++t)
+            for (int ph = 0; ph < 8; ++ph)
+                for (int i = 0; i < count; ++i) {
+                    ba.phase_begin = ph;
+                    ba.phase_end = ph + 1;
+                    ba.inst_begin = i;
+                    const int64_t items = hoff[(size_t)ph * (count + 1) + i + 1] -
+                                          hoff[(size_t)ph * (count + 1) + i];
+                    CK(launch_batched(ba, (int)items, false, s));
+                }
+    }
+    CK(cudaEventRecord(e1, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    unsigned long long inner = 0;
+    CK(cudaMemcpy(&inner, h->ctr + 1, sizeof(inner), cudaMemcpyDeviceToHost));
+    if (reps) {
+        double rows_total = 0.0;
+        for (int i = 0; i < count; ++i)
+            rows_total += (double)(inst[i].m + inst[i].n);
+        for (int i = 0; i < count; ++i) {
+            nmf_dense Vd{inst[i].m, inst[i].n, inst[i].n, NMF_F32, inst[i].V};
+            double *Jd = h->scal + 8;
+            nmf_status e = nmf_objective_direct(h, &Vd, inst[i].W, inst[i].Ht, inst[i].r,
+                                                opts->alpha_w, opts->alpha_h, opts->beta_w,
+                                                opts->beta_h, Jd);
+            if (e)
+                return e;
+            double J = 0.0;
+            CK(cudaMemcpyAsync(&J, Jd, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            reps[i] = nmf_report{};
+            reps[i].iters_done = opts->outer_iters;
+            reps[i].objective = J;
+            reps[i].ms_total = ms;
+            reps[i].inner_total = (int64_t)inner;
+            reps[i].kbar = opts->outer_iters > 0 ? (double)inner / (opts->outer_iters * rows_total)
+                                                 : 0.0;
+        }
+    }
+    return nmf_sync(h);
+}
 
 // ---------------------------------------------------------------------------
 // projection onto a fixed basis

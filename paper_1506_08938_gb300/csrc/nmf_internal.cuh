@@ -30,6 +30,7 @@ struct ProfScope {
     ~ProfScope() { prof_mark(cls, s, false); }
 };
 void prof_suspend(bool on);   // no events while a stream is being captured
+void prof_thread_off();       // this host thread never records profiler events
 
 // ---- NNLS (Alg. 3) --------------------------------------------------------
 struct NnlsArgs {
@@ -97,6 +98,37 @@ cudaError_t launch_tc_pack(const float *X, int64_t K, int r, int mode, void *pac
 cudaError_t launch_tc_cross(const void *A, int64_t M, int64_t K, int64_t lda, int r, int mode,
                             const void *pack, float *P, const TcPlan &pl, unsigned *status,
                             cudaStream_t s);
+
+// ---- batched instances (one launch per outer iteration) -------------------
+struct BatchInst {
+    int64_t m, n;
+    int r;
+    const float *V, *Vt;
+    float *W, *Ht;
+    float *gram, *Qt, *d, *Cw, *Ch;
+    float alpha_w, alpha_h, beta_w, beta_h;
+};
+struct BatchNnls {
+    int max_inner;
+    float eps;
+    int cd_steps;
+};
+struct BatchArgs {
+    const BatchInst *inst;     // device array [count]
+    int count;
+    const int64_t *item_off;   // device [8][count + 1]: prefix sums of work items
+    int phase_begin, phase_end;
+    int inst_begin;            // -1: all instances; else one instance
+    int nnls_rows;             // rows per NNLS work item
+    BatchNnls nnls;
+    unsigned long long *iter_total;
+    unsigned *status;
+    unsigned *bar_count, *bar_gen;
+};
+size_t batched_smem_bytes();
+int64_t batched_items(int phase, int64_t m, int64_t n, int nnls_rows);
+int batched_grid(bool cooperative);
+cudaError_t launch_batched(const BatchArgs &a, int grid, bool cooperative, cudaStream_t s);
 
 // ---- sparse cross term ----------------------------------------------------
 struct SpmmPlan {

@@ -65,6 +65,7 @@ def test_argument_errors_return_before_launch(lib):
                                None) == P.NMF_E_ARG
     assert lib.nmf_solve(None, None, None, 4, None, None, None, None) == P.NMF_E_ARG
     assert lib.nmf_project(None, None, None, None, 0, 4, None, None, None) == P.NMF_E_ARG
+    assert lib.nmf_solve_batched(None, 1, None, None, 0, None) == P.NMF_E_ARG
     assert lib.nmf_destroy(None) == P.NMF_E_ARG
     assert lib.nmf_create(None, 0, None) == P.NMF_E_ARG
     assert P.launch_count() == before

@@ -106,3 +106,29 @@ def test_tc_and_simt_solves_agree(h):
         P.nmf_solve(h, V, W, Ht, o)
         out.append((to_np(W), to_np(Ht), hist.copy()))
     assert np.abs(out[0][2] - out[1][2]).max() / out[1][2].max() < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_reduced_precision_solves_track_fp32(h, prec):
+    """Solve with TF32 / BF16 cross terms (FP32 accumulation; Grams and NNLS
+    in FP32) against the FP32 solve from the same start, on the non-chaotic
+    instance (L2 weight 10).  Stated bound: the products carry relative
+    errors up to 6.5e-4 (TF32) and 2e-4 (BF16, measured above); the
+    objectives over 20 iterations agree to 2e-3 and decrease monotonically."""
+    import ctypes as C
+    inst = WL.tiny(seed=0, r=10, m=200, n=152)     # n multiple of 8 for BF16 rows
+    Vd = t32(inst.V)
+    out = {}
+    for p_ in ("fp32", prec):
+        W = t32(inst.W0)
+        Ht = t32(inst.Ht0)
+        hist = np.zeros(20)
+        o = P.solve_opts(20, beta_w=10.0, beta_h=10.0, prec=p_, objective="direct",
+                         nnls=P.nnls_opts(max_inner=3, eps=0.0),
+                         obj_hist=hist.ctypes.data_as(C.POINTER(C.c_double)))
+        P.nmf_solve(h, Vd, W, Ht, o)
+        out[p_] = hist.copy()
+    rel = np.abs(out[prec] - out["fp32"]) / out["fp32"]
+    print(f"{prec} vs fp32 max rel J {rel.max():.3e}")
+    assert rel.max() < 2e-3, rel
+    assert np.all(np.diff(out[prec]) <= 1e-6 * out[prec][1:])

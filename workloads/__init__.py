@@ -145,10 +145,10 @@ def zipf_rows(g: np.random.Generator, counts: np.ndarray, n: int, s: float = 1.1
     cdf[-1] = 1.0
     out: list[np.ndarray] = [None] * len(counts)  # type: ignore
     kmax = int(counts.max()) if len(counts) else 0
-    ndraw = max(64, 4 * kmax)
     for a in range(0, len(counts), chunk):
         b = min(len(counts), a + chunk)
         pending = np.arange(a, b)
+        ndraw = max(64, 4 * kmax)   # doubled only for the rows still short
         while len(pending):
             d = np.searchsorted(cdf, g.random((len(pending), ndraw)), side="right")
             d = np.minimum(d, n - 1)
@@ -227,22 +227,38 @@ def random_csr(seed: int, m: int, n: int, density: float, empty_rows: int = 0,
 
 
 def batched(seed: int = 0, count: int = 256, m_range=(100, 4000), n_range=(100, 2000),
-            ranks=(8, 16, 32, 64), outer_iters: int = 100) -> list[DenseInstance]:
-    """Independent dense instances of uneven shape, V = W0 H0 + |N(0,0.01)|."""
+            ranks=(8, 16, 32, 64), outer_iters: int = 100,
+            workers: int = 1) -> list[DenseInstance]:
+    """Independent dense instances of uneven shape, V = W0 H0 + |N(0,0.01)|
+    with W0, H0 and the initial factors U[0,1] (all FP32; the noise drawn as
+    single-precision normals).  Shapes come from one stream of ``seed``;
+    instance i's values from its own child stream, so ``workers`` threads
+    give the same instances as one."""
     g = rng(seed)
-    out = []
-    for i in range(count):
+    shapes = []
+    for _ in range(count):
         m = int(g.integers(m_range[0], m_range[1] + 1))
         n = int(g.integers(n_range[0], n_range[1] + 1))
         r = int(ranks[int(g.integers(0, len(ranks)))])
-        W0 = g.random((m, r), dtype=np.float32)
-        H0 = g.random((r, n), dtype=np.float32)
-        V = (W0 @ H0 + _abs_noise(g, (m, n)).astype(np.float32)).astype(np.float32)
-        Wi = g.random((m, r), dtype=np.float32)
-        Hti = g.random((n, r), dtype=np.float32)
-        out.append(DenseInstance(V, Wi, Hti, r, outer_iters=outer_iters,
-                                 name=f"b{i}_{m}x{n}r{r}"))
-    return out
+        shapes.append((m, n, r))
+    children = np.random.SeedSequence(int(seed)).spawn(count)
+
+    def make(i):
+        m, n, r = shapes[i]
+        gi = np.random.default_rng(children[i])
+        W0 = gi.random((m, r), dtype=np.float32)
+        H0 = gi.random((r, n), dtype=np.float32)
+        noise = np.abs(gi.standard_normal((m, n), dtype=np.float32)) * np.float32(0.01)
+        V = W0 @ H0 + noise
+        Wi = gi.random((m, r), dtype=np.float32)
+        Hti = gi.random((n, r), dtype=np.float32)
+        return DenseInstance(V, Wi, Hti, r, outer_iters=outer_iters, name=f"b{i}_{m}x{n}r{r}")
+
+    if workers > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(workers) as ex:
+            return list(ex.map(make, range(count)))
+    return [make(i) for i in range(count)]
 
 
 @dataclass
