@@ -109,6 +109,8 @@ typedef struct {
                             the largest final ||f||^2 of the previous update of
                             the same factor (deterministic reading) [0]       */
     float maxstop;       /* threshold for mode 1 in nmf_nnls_update [0]       */
+    int lanes;           /* lanes of a warp per row problem: 1, 2, 4, ..., 32
+                            with lanes * 8 >= r; 0 = chosen from r [0]        */
 } nmf_nnls_opts;
 
 /* Options of the outer loop (Alg. 1 / Alg. 2). */

@@ -48,7 +48,7 @@ class Matrix(C.Structure):
 
 class NnlsOpts(C.Structure):
     _fields_ = [("max_inner", C.c_int), ("eps", C.c_double), ("cd_steps", C.c_int),
-                ("maxstop_mode", C.c_int), ("maxstop", C.c_float)]
+                ("maxstop_mode", C.c_int), ("maxstop", C.c_float), ("lanes", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -212,8 +212,10 @@ def matrix_csr(rowptr, colidx, vals, ncols: int) -> Matrix:
     return m
 
 
-def nnls_opts(max_inner=50, eps=1e-3, cd_steps=-1, maxstop_mode=0, maxstop=0.0) -> NnlsOpts:
-    return NnlsOpts(int(max_inner), float(eps), int(cd_steps), int(maxstop_mode), float(maxstop))
+def nnls_opts(max_inner=50, eps=1e-3, cd_steps=-1, maxstop_mode=0, maxstop=0.0,
+              lanes=0) -> NnlsOpts:
+    return NnlsOpts(int(max_inner), float(eps), int(cd_steps), int(maxstop_mode), float(maxstop),
+                    int(lanes))
 
 
 def solve_opts(outer_iters, rel_gap_target=0.0, f_star=0.0, alpha_w=0.0, alpha_h=0.0,

@@ -277,6 +277,7 @@ NMF_API void nmf_nnls_opts_default(nmf_nnls_opts *o)
     o->cd_steps = -1;
     o->maxstop_mode = 0;
     o->maxstop = 0.f;
+    o->lanes = 0;
 }
 
 NMF_API int64_t nmf_launch_count(void) { return g_launches.load(); }
@@ -356,6 +357,8 @@ NMF_API nmf_status nmf_sync(nmf_handle h)
         CK(cudaMemset(h->status, 0, sizeof(unsigned)));
         if (st & kStTimeout)
             return NMF_E_TIMEOUT;
+        if (st & kStBadInput)
+            return NMF_E_ARG;
         return NMF_E_NONFINITE;
     }
     return NMF_OK;
@@ -504,6 +507,9 @@ NMF_API nmf_status nmf_nnls_update(nmf_handle h, const float *Qt, const float *d
     nmf_nnls_opts o = opts_or_default(opts);
     if (o.maxstop_mode < 0 || o.maxstop_mode > 1)
         return NMF_E_ARG;
+    int lg = 0, lj = 0;
+    if (!nnls_layout(r, o.lanes, &lg, &lj))
+        return NMF_E_ARG;
     NnlsArgs a{};
     a.Qt = Qt;
     a.d = d;
@@ -519,6 +525,7 @@ NMF_API nmf_status nmf_nnls_update(nmf_handle h, const float *Qt, const float *d
     a.cd_steps = o.cd_steps;
     a.maxstop_mode = o.maxstop_mode;
     a.maxstop = o.maxstop;
+    a.lanes = o.lanes;
     a.iters = inner_iters;
     a.status = h->status;
     CK(launch_nnls(a, h->stream));
@@ -675,6 +682,7 @@ nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, const float *Gother)
     a.cd_steps = L.nn.cd_steps;
     a.maxstop_mode = L.nn.maxstop_mode;
     a.maxstop = 0.f;
+    a.lanes = L.nn.lanes;
     a.iter_total = h->ctr;
     a.status = h->status;
     if (L.nn.maxstop_mode == 1)
@@ -881,6 +889,11 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     L.nn = opts_or_default(&o.nnls);
     if (L.nn.maxstop_mode != 0)
         return NMF_E_NOTIMPL;
+    {
+        int lg = 0, lj = 0;
+        if (!nnls_layout(r, L.nn.lanes, &lg, &lj))
+            return NMF_E_ARG;
+    }
     int64_t m, n;
     const bool sparse = V->is_sparse != 0;
     if (sparse) {
@@ -1102,7 +1115,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     long long per_iter_launches = 0;
-    CK(prepare_nnls(r));
+    CK(prepare_nnls(r, L.nn.lanes));
     if (o.use_graph && o.outer_iters > 0) {
         if (!h->cap)
             CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));

@@ -1,0 +1,520 @@
+// Batched NQP solver: Alg. 3 of §3.4 (anti-lopsided rescaled problem, exact
+// line search along the masked gradient, then greedy coordinate descent) for
+// many rows that share one rescaled Gram matrix Qt.
+//
+// Qt comes from the rescale step, so its diagonal is exactly 1 on live
+// coordinates and its dead rows and columns are zero; the 1-D minimiser of
+// coordinate p then moves y_p by del = max(-y_p, -g_p), which lowers the
+// objective by -del (g_p + del / 2).  A Qt whose diagonal holds anything but
+// 0 or 1 is rejected (status flag, X untouched).
+//
+// Layout.  A group of G consecutive lanes owns one row problem, so a warp
+// works on 32/G rows at once.  Lane li of a group holds J coordinates of the
+// gradient g in registers, in chunks of CW = min(J, 4) consecutive
+// coordinates: chunk c covers (c*G + li)*CW ... +CW-1, so that the G lanes of
+// a group read one contiguous run of any Qt row (no shared-memory bank
+// conflicts).  RP = G*J >= r.  The iterate y of each group lives in shared
+// memory in coordinate order: a coordinate step changes one entry, which its
+// owner lane rewrites, and every lane reloads its chunks at the next step.
+// Qt, zero-padded to RP x RP, is loaded once per CTA; it is symmetric, so the
+// column Qt[:, p] a coordinate step needs is read as the contiguous row p.
+//
+// Per coordinate step a lane evaluates the gains of its J coordinates, the
+// group takes the maximum key with log2(G) xor-shuffles, and a ballot names
+// the lowest lane holding it; within a lane the lower index wins, so exact
+// ties go to the lowest coordinate, as in the oracle.
+//
+// Scheduling.  The groups of a warp run in lockstep but on their own rows:
+// the warp loops over rounds, each round = (start rows in groups that are
+// free) + one iteration of Alg. 3's repeat loop (line search and the
+// coordinate steps) for every busy group + the stop test.  A group whose row
+// meets the stop rule writes it out and takes the next row of the warp's
+// share in the next round, so a row that needs many iterations does not hold
+// up its neighbours.  Idle groups ride along with zero steps, which leave
+// their state unchanged.
+#pragma once
+#include "nmf_internal.cuh"
+
+namespace nmfi {
+namespace nnls_detail {
+
+constexpr int kWarps = 8;
+constexpr unsigned kFull = 0xffffffffu;
+// keys are the bits of -gain <= 0 read as unsigned: a positive gain maps above
+// this value, a zero gain (either sign of zero) to it or below
+constexpr unsigned kNoGain = 0x80000000u;
+
+template <int G, int J>
+struct Map {
+    static constexpr int CW = J < 4 ? J : 4;   // chunk width
+    static constexpr int NC = J / CW;          // chunks per lane
+    static constexpr int RP = G * J;
+    static constexpr int VB = RP + 4;          // per-group buffer stride (16-byte aligned)
+    __device__ static __forceinline__ int coord(int li, int j)
+    {
+        return ((j / CW) * G + li) * CW + (j % CW);
+    }
+};
+
+// a lane's J values of a length-RP row p (coordinate order)
+template <int G, int J>
+__device__ __forceinline__ void ld_lane(const float *p, int li, float (&a)[J])
+{
+    using M = Map<G, J>;
+#pragma unroll
+    for (int c = 0; c < M::NC; ++c) {
+        const float *q = p + (c * G + li) * M::CW;
+        if constexpr (M::CW == 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(q);
+            a[4 * c] = t.x; a[4 * c + 1] = t.y; a[4 * c + 2] = t.z; a[4 * c + 3] = t.w;
+        } else {
+            const float2 t = *reinterpret_cast<const float2 *>(q);
+            a[2 * c] = t.x; a[2 * c + 1] = t.y;
+        }
+    }
+}
+
+template <int G, int J>
+__device__ __forceinline__ void st_lane(float *p, int li, const float (&a)[J])
+{
+    using M = Map<G, J>;
+#pragma unroll
+    for (int c = 0; c < M::NC; ++c) {
+        float *q = p + (c * G + li) * M::CW;
+        if constexpr (M::CW == 4)
+            *reinterpret_cast<float4 *>(q) =
+                make_float4(a[4 * c], a[4 * c + 1], a[4 * c + 2], a[4 * c + 3]);
+        else
+            *reinterpret_cast<float2 *>(q) = make_float2(a[2 * c], a[2 * c + 1]);
+    }
+}
+
+// sum over the G lanes of a group (aligned groups: xor offsets < G stay inside)
+template <int G>
+__device__ __forceinline__ float group_sum(float v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1)
+        v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_max(unsigned v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        unsigned w = __shfl_xor_sync(kFull, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// all G ballot bits of one group set
+template <int G>
+__host__ __device__ constexpr unsigned group_full()
+{
+    if constexpr (G == 32)
+        return kFull;
+    else
+        return (1u << G) - 1u;
+}
+
+// the G ballot bits of group gi
+template <int G>
+__device__ __forceinline__ unsigned group_bits(unsigned ballot, int gi)
+{
+    if constexpr (G == 32)
+        return ballot;
+    else
+        return (ballot >> (gi * G)) & group_full<G>();
+}
+
+// out = Qt v for every group of the warp at once, v read from the group's
+// buffer vg (coordinate order, broadcast float4); only the first
+// r4 = roundup(r, 4) rows of Qt are non-zero.
+template <int G, int J>
+__device__ __forceinline__ void matvec_buf(const float *__restrict__ Qs, const float *vg,
+                                           float (&out)[J], int li, int r4)
+{
+    constexpr int RP = Map<G, J>::RP;
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+        out[j] = 0.f;
+    for (int k = 0; k < r4; k += 4) {
+        const float4 vk = *reinterpret_cast<const float4 *>(vg + k);
+        float a0[J], a1[J];
+        ld_lane<G, J>(Qs + k * RP, li, a0);
+        ld_lane<G, J>(Qs + (k + 1) * RP, li, a1);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            out[j] = fmaf(a0[j], vk.x, out[j]);
+            out[j] = fmaf(a1[j], vk.y, out[j]);
+        }
+        ld_lane<G, J>(Qs + (k + 2) * RP, li, a0);
+        ld_lane<G, J>(Qs + (k + 3) * RP, li, a1);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            out[j] = fmaf(a0[j], vk.z, out[j]);
+            out[j] = fmaf(a1[j], vk.w, out[j]);
+        }
+    }
+}
+
+// stage v (a lane's J values) in the group buffer vbg, then out = Qt v
+template <int G, int J>
+__device__ __forceinline__ void matvec(const float *__restrict__ Qs, float *vbg,
+                                       const float (&v)[J], float (&out)[J], int li, int r4)
+{
+    st_lane<G, J>(vbg, li, v);
+    __syncwarp();
+    matvec_buf<G, J>(Qs, vbg, out, li, r4);
+    __syncwarp();
+}
+
+// this lane's part of ||P(y, g)||^2: the passive set is {y > 0 or g < 0}
+template <int J>
+__device__ __forceinline__ float proj_part(const float (&y)[J], const float (&g)[J])
+{
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+        if (y[j] > 0.f || g[j] < 0.f)
+            s = fmaf(g[j], g[j], s);
+    return s;
+}
+
+template <int G, int J>
+constexpr size_t smem_bytes()
+{
+    using M = Map<G, J>;
+    return sizeof(float) *
+           ((size_t)M::RP * M::RP + M::RP + 2 * (size_t)kWarps * (32 / G) * M::VB);
+}
+
+// CTAs per SM the register budget is sized for
+template <int J>
+constexpr int min_ctas() { return J >= 4 ? 3 : 4; }
+
+template <int G, int J>
+__global__ void __launch_bounds__(kWarps * 32, min_ctas<J>()) k_nnls(const NnlsArgs a)
+{
+    using M = Map<G, J>;
+    constexpr int RP = M::RP;
+    constexpr int NG = 32 / G;            // rows per warp
+    extern __shared__ __align__(16) float smem[];
+    float *Qs = smem;                     // RP x RP
+    float *sd = Qs + RP * RP;             // scale d (1 for dead and padding)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gi = lane / G, li = lane - gi * G;
+    float *vbg = sd + RP + (warp * NG + gi) * M::VB;                        // staging
+    float *ysg = sd + RP + (kWarps * NG + warp * NG + gi) * M::VB;          // iterate y
+    const int r = a.r;
+    const int r4 = (r + 3) & ~3;
+
+    for (int idx = threadIdx.x; idx < RP * RP; idx += blockDim.x) {
+        int i = idx / RP, j = idx - i * RP;
+        Qs[idx] = (i < r && j < r) ? a.Qt[i * r + j] : 0.f;
+    }
+    __syncthreads();
+    bool bad = false;
+    for (int e = threadIdx.x; e < RP; e += blockDim.x) {
+        const float qii = Qs[e * RP + e];
+        bad = bad || (qii != 0.f && qii != 1.f);
+        sd[e] = (e < r && qii > 0.f) ? a.d[e] : 1.f;
+    }
+    if (__syncthreads_or(bad)) {
+        if (threadIdx.x == 0 && a.status)
+            atomicOr(a.status, kStBadInput);
+        return;
+    }
+
+    // live coordinates (bit j: this lane's j-th); a dead one keeps y = g = 0
+    unsigned live = 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int e = M::coord(li, j);
+        if (e < r && Qs[e * RP + e] > 0.f)
+            live |= 1u << j;
+    }
+    const int T = a.cd_steps < 0 ? r : a.cd_steps;
+    const int64_t nw = (int64_t)gridDim.x * kWarps;
+    int64_t next = (int64_t)blockIdx.x * kWarps + warp;   // this warp's rows: next, next + nw, ...
+    const unsigned below = (1u << (gi * G)) - 1u;          // ballot bits of the groups before gi
+
+    float g[J], zero[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+        g[j] = zero[j] = 0.f;
+    st_lane<G, J>(ysg, li, zero);
+    int64_t row = -1;
+    bool active = false, need = true;
+    int k = 0;
+    float s0 = 0.f;
+    unsigned my_iters = 0;
+    unsigned my_smax = 0;
+
+    auto finish = [&](float sk) {
+        float y[J];
+        ld_lane<G, J>(ysg, li, y);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int e = M::coord(li, j);
+            if (e < r)
+                a.X[row * r + e] = ((live >> j) & 1u) ? y[j] / sd[e] : 0.f;
+        }
+        if (li == 0) {
+            if (a.iters)
+                a.iters[row] = k;
+            my_iters += (unsigned)k;
+            const unsigned sb = __float_as_uint(sk);
+            my_smax = sb > my_smax ? sb : my_smax;
+        }
+        st_lane<G, J>(ysg, li, zero);
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            g[j] = 0.f;
+    };
+
+    for (;;) {
+        // ---- free groups take the next rows of this warp's share, in group order
+        const unsigned needb = __ballot_sync(kFull, need && li == 0);
+        bool fresh = false;
+        if (need) {
+            const int64_t cand = next + (int64_t)__popc(needb & below) * nw;
+            row = cand < a.rows ? cand : -1;
+            fresh = row >= 0;
+            need = false;   // busy now, or the share is exhausted: idle for good
+        }
+        next += (int64_t)__popc(needb) * nw;
+        if (!__any_sync(kFull, fresh || active))
+            break;
+
+        // ---- start fresh rows: y = x0 .* d, g = Qt y + (alpha - c) ./ d
+        if (__any_sync(kFull, fresh)) {
+            bool ok = true;
+            if (fresh) {
+                float y0[J];
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const int e = M::coord(li, j);
+                    float c = 0.f, x0 = 0.f;
+                    if (e < r) {
+                        const float *cp = a.C + row * r + e;
+                        for (int s = 0; s < a.nsplit; ++s)
+                            c += cp[s * a.c_stride];
+                        x0 = a.X[row * r + e];
+                        ok = ok && isfinite(c) && isfinite(x0);
+                    }
+                    const bool lv = (live >> j) & 1u;
+                    g[j] = lv ? (a.alpha - c) / sd[e] : 0.f;   // q staged in g
+                    y0[j] = lv ? x0 * sd[e] : 0.f;
+                }
+                st_lane<G, J>(ysg, li, y0);
+            }
+            const bool gok = group_bits<G>(__ballot_sync(kFull, ok), gi) == group_full<G>();
+            __syncwarp();
+            float t[J];
+            matvec_buf<G, J>(Qs, ysg, t, li, r4);   // busy groups' products are not used
+            __syncwarp();
+            if (fresh) {
+#pragma unroll
+                for (int j = 0; j < J; ++j)
+                    g[j] = (gok && ((live >> j) & 1u)) ? g[j] + t[j] : 0.f;
+                if (!gok)
+                    st_lane<G, J>(ysg, li, zero);
+            }
+            float y[J];
+            ld_lane<G, J>(ysg, li, y);
+            const float s0n = group_sum<G>(proj_part<J>(y, g));
+            if (fresh) {
+                if (!gok) {
+                    if (li == 0 && a.status)
+                        atomicOr(a.status, kStNonFinite);
+                    need = true;   // row skipped, X left as it was
+                } else if (s0n > 0.f) {
+                    active = true;
+                    s0 = s0n;
+                    k = 0;
+                } else {           // already optimal: k = 0
+                    k = 0;
+                    finish(s0n);
+                    need = true;
+                }
+            }
+        }
+
+        // ---- exact line search along the masked gradient (busy groups)
+        {
+            float y[J], gb[J];
+            ld_lane<G, J>(ysg, li, y);
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                gb[j] = (active && (y[j] > 0.f || g[j] < 0.f)) ? g[j] : 0.f;
+                s = fmaf(gb[j], gb[j], s);
+            }
+            s = group_sum<G>(s);
+            if (__any_sync(kFull, s > 0.f)) {
+                float u[J];
+                matvec<G, J>(Qs, vbg, gb, u, li, r4);
+                float den = 0.f;
+#pragma unroll
+                for (int j = 0; j < J; ++j)
+                    den = fmaf(gb[j], u[j], den);
+                den = group_sum<G>(den);
+                const float al = (s > 0.f && den > 0.f) ? s / den : 0.f;
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const float yn = fmaxf(0.f, y[j] - al * gb[j]);
+                    gb[j] = yn - y[j];   // the step actually taken
+                    y[j] = yn;
+                }
+                st_lane<G, J>(ysg, li, y);
+                matvec<G, J>(Qs, vbg, gb, u, li, r4);
+#pragma unroll
+                for (int j = 0; j < J; ++j)
+                    g[j] += u[j];
+            }
+        }
+
+        // ---- greedy coordinate descent: T steps of the largest decrease
+        for (int t = 0; t < T; ++t) {
+            float y[J];
+            ld_lane<G, J>(ysg, li, y);
+            unsigned key[J];
+            int idx[J];
+            float del[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                // dead or padding coordinates have y = g = 0: del = 0, no gain
+                del[j] = fmaxf(-y[j], -g[j]);
+                key[j] = __float_as_uint(del[j] * fmaf(0.5f, del[j], g[j]));   // = -gain
+                idx[j] = j;
+            }
+#pragma unroll
+            for (int s = 1; s < J; s <<= 1)
+#pragma unroll
+                for (int j = 0; j + s < J; j += 2 * s)
+                    if (key[j + s] > key[j]) {   // strict: the lower index keeps ties
+                        key[j] = key[j + s];
+                        idx[j] = idx[j + s];
+                        del[j] = del[j + s];
+                    }
+            const unsigned bkey = active ? key[0] : 0u;
+            const unsigned m = group_max<G>(bkey);
+            const bool step = m > kNoGain;
+            if (!__any_sync(kFull, step))
+                break;
+            const unsigned wb = group_bits<G>(__ballot_sync(kFull, bkey == m), gi);
+            const int sli = __ffs(wb) - 1;
+            const int src = gi * G + sli;
+            const int pj = __shfl_sync(kFull, idx[0], src);
+            float dp = __shfl_sync(kFull, del[0], src);
+            dp = step ? dp : 0.f;   // no positive gain: this group takes no step
+            const int p = M::coord(sli, pj);
+            float col[J];
+            ld_lane<G, J>(Qs + p * RP, li, col);
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+                g[j] = fmaf(col[j], dp, g[j]);
+            if (step && lane == src)
+                ysg[p] += dp;
+        }
+
+        // ---- stop test (Alg. 3): accelerated condition, fast break, cap
+        float y[J];
+        ld_lane<G, J>(ysg, li, y);
+        const float sk = group_sum<G>(proj_part<J>(y, g));
+        if (active) {
+            ++k;
+            const bool stop = sk <= a.eps * s0 || (a.maxstop_mode == 1 && sk <= a.maxstop) ||
+                              k >= a.max_inner;
+            if (stop) {
+                finish(sk);
+                active = false;
+                need = true;
+            }
+        }
+    }
+    if (li == 0) {
+        if (a.iter_total && my_iters)
+            atomicAdd(a.iter_total, (unsigned long long)my_iters);
+        if (a.s_final_max && my_smax)
+            atomicMax(a.s_final_max, my_smax);
+    }
+}
+
+template <int G, int J>
+struct Cfg {
+    static int blocks_per_sm, sms;
+};
+template <int G, int J>
+int Cfg<G, J>::blocks_per_sm = -1;
+template <int G, int J>
+int Cfg<G, J>::sms = 0;
+
+// one-time launch configuration (kept out of any stream capture)
+template <int G, int J>
+cudaError_t prepare()
+{
+    const size_t smem = smem_bytes<G, J>();
+    int &bps = Cfg<G, J>::blocks_per_sm, &sms = Cfg<G, J>::sms;
+    if (bps < 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_nnls<G, J>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_nnls<G, J>, kWarps * 32, smem);
+        if (e != cudaSuccess)
+            return e;
+        if (bps < 1)
+            bps = 1;
+    }
+    return cudaSuccess;
+}
+
+template <int G, int J>
+cudaError_t launch(const NnlsArgs &a, cudaStream_t s)
+{
+    cudaError_t e = prepare<G, J>();
+    if (e != cudaSuccess)
+        return e;
+    constexpr int rows_per_cta = kWarps * (32 / G);
+    const int64_t need = (a.rows + rows_per_cta - 1) / rows_per_cta;
+    const int64_t cap = (int64_t)Cfg<G, J>::blocks_per_sm * Cfg<G, J>::sms;
+    const int grid = (int)(need < cap ? need : cap);
+    if (grid < 1)
+        return cudaSuccess;
+    k_nnls<G, J><<<grid, kWarps * 32, smem_bytes<G, J>(), s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// all lane counts for one J
+template <int J>
+cudaError_t dispatch(const NnlsArgs &a, int G, bool prep_only, cudaStream_t s)
+{
+    switch (G) {
+    case 1: return prep_only ? prepare<1, J>() : launch<1, J>(a, s);
+    case 2: return prep_only ? prepare<2, J>() : launch<2, J>(a, s);
+    case 4: return prep_only ? prepare<4, J>() : launch<4, J>(a, s);
+    case 8: return prep_only ? prepare<8, J>() : launch<8, J>(a, s);
+    case 16: return prep_only ? prepare<16, J>() : launch<16, J>(a, s);
+    case 32: return prep_only ? prepare<32, J>() : launch<32, J>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace nnls_detail
+
+// per-J entry points (one translation unit each)
+cudaError_t nnls_dispatch_j2(const NnlsArgs &a, int G, bool prep_only, cudaStream_t s);
+cudaError_t nnls_dispatch_j4(const NnlsArgs &a, int G, bool prep_only, cudaStream_t s);
+cudaError_t nnls_dispatch_j8(const NnlsArgs &a, int G, bool prep_only, cudaStream_t s);
+
+}  // namespace nmfi

@@ -14,14 +14,15 @@
 //    ring of stages tracked by mbarriers.  Warp 1 (one thread) issues
 //    tcgen05.mma into a TMEM accumulator (128 lanes x N columns, FP32) and
 //    commits each stage back to the producer.  The accumulator is double
-//    buffered in TMEM: every chunk of k blocks goes to one buffer while warps
-//    2-9 read the other through tcgen05.ld and add it into FP32 registers
-//    (round to nearest), so the tensor core's truncating accumulation never
-//    runs over more than one chunk.
+//    buffered in TMEM: every chunk of k blocks goes to one buffer while the
+//    accumulating warps read the other through tcgen05.ld and add it into
+//    FP32 registers (round to nearest), so the tensor core's truncating
+//    accumulation never runs over more than one chunk.
 //  * Arithmetic.  TF32: one MMA per k step.  TF32X3 (FP32-accurate): the
 //    tensor core's TF32 conversion truncates, so the A tile serves as its own
-//    high part and warps 2-9 write the TF32-rounded remainder A - trunc(A)
-//    to a small ring; the packed factor stacks its TF32 high part over its
+//    high part and warps 2-5 write the TF32-rounded remainder A - trunc(A)
+//    to a small ring while warps 6-9 accumulate (the two jobs overlap instead
+//    of taking turns); the packed factor stacks its TF32 high part over its
 //    TF32 remainder, so one N = 2 NPAD MMA gives A*B_hi and A*B_lo side by
 //    side in TMEM and a second (N = NPAD) adds A_lo*B_hi.  BF16: A and B in
 //    BF16, kind::f16.
@@ -39,6 +40,7 @@ namespace {
 
 constexpr int kThreads = 320;     // producer, MMA, 8 split/accumulate warps
 constexpr int kEpi = 256;         // threads of warps 2..9
+constexpr int kSplit = 128;       // TF32X3: warps 2..5 split, warps 6..9 accumulate
 constexpr uint32_t kABytes = 128 * 128;   // 128 rows x 128 bytes
 constexpr unsigned long long kDeadlineNs = 2000000000ull;   // 2 s, a kernel takes < 1 ms
 
@@ -208,6 +210,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                const TcArgs p)
 {
     constexpr bool X3 = MODE == TC_TF32X3;
+    // TF32X3 with NPAD <= 64: warps 2-5 split while warps 6-9 accumulate.
+    // Wider factors keep all eight warps on both jobs (an accumulating thread
+    // could not hold 2 x 128 columns).
+    constexpr bool SR = X3 && NPAD <= 64;
+    constexpr int SPLIT_T = SR ? kSplit : kEpi;   // threads that split
     constexpr int NB = X3 ? 2 * NPAD : NPAD;                  // rows of the packed factor tile
     constexpr uint32_t B_BYTES = NB * 128;
     constexpr uint32_t STAGE_BYTES = kABytes + B_BYTES;
@@ -236,6 +243,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t it0 = (int64_t)blockIdx.x * p.iters / p.grid;
     const int64_t it1 = (int64_t)(blockIdx.x + 1) * p.iters / p.grid;
     const int KB = p.kblocks;
+    // (row tile, k block) of it0; every role then steps both counters (a
+    // 64-bit division per iteration would sit on the single-thread paths)
+    const int tile0 = (int)(it0 / KB), kb0 = (int)(it0 - (int64_t)tile0 * KB);
     const unsigned long long deadline = gtimer() + kDeadlineNs;
 
     if (threadIdx.x == 0) {
@@ -244,12 +254,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&empty[s], 1);
         }
         for (int j = 0; j < NLO; ++j) {
-            mbar_init(&lo_full[j], kEpi);
+            mbar_init(&lo_full[j], SPLIT_T);
             mbar_init(&lo_empty[j], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], kEpi);
+            mbar_init(&acc_empty[b], SR ? kEpi - kSplit : kEpi);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -272,8 +282,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
+            int tile = tile0, kb = kb0 - 1;
             for (int64_t it = it0; it < it1; ++it) {
-                const int tile = (int)(it / KB), kb = (int)(it % KB);
+                if (++kb == KB) {
+                    kb = 0;
+                    ++tile;
+                }
                 if (!mbar_wait(&empty[stage], phase ^ 1u, deadline, abort_flag))
                     break;
                 mbar_expect_tx(&full[stage], TX_BYTES);
@@ -301,8 +315,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             int stage = 0, buf = 0, pos = 0, lo = 0;
             uint32_t phase = 0, lo_phase = 0, uses0 = 0, uses1 = 0;
+            int kb = kb0 - 1;
             for (int64_t it = it0; it < it1; ++it) {
-                const int kb = (int)(it % KB);
+                if (++kb == KB)
+                    kb = 0;
                 const bool seg_start = it == it0 || kb == 0;
                 const bool seg_end = it + 1 == it1 || kb == KB - 1;
                 pos = seg_start ? 0 : pos + 1;
@@ -356,28 +372,69 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+    } else if (SR && warp < 6) {
+        // ---------------- TF32X3 split: warps 2..5, 128 threads.  The tensor
+        // core reads A through its TF32 conversion, which truncates, so A
+        // itself acts as the high part and the remainder A - trunc(A),
+        // rounded to TF32, is written to the low ring.  The MMA of a stage
+        // waits for its low part, so the stage (and A in it) stays valid here.
+        const int t = threadIdx.x - 64;   // 0..127
+        int stage = 0, lo = 0;
+        uint32_t phase = 0, lo_phase = 0;
+        for (int64_t it = it0; it < it1; ++it) {
+            // warp-uniform decisions: every lane of the warp continues or none
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, deadline, abort_flag)))
+                break;
+            if (!__all_sync(0xffffffffu,
+                            mbar_wait(&lo_empty[lo], lo_phase ^ 1u, deadline, abort_flag)))
+                break;
+            const float4 *a4 = reinterpret_cast<const float4 *>(A(stage));
+            float4 *l4 = reinterpret_cast<float4 *>(LO(lo));
+            float4 v[kABytes / 16 / kSplit];
+#pragma unroll
+            for (int q = 0; q < (int)(kABytes / 16 / kSplit); ++q)
+                v[q] = a4[t + kSplit * q];
+#pragma unroll
+            for (int q = 0; q < (int)(kABytes / 16 / kSplit); ++q) {
+                float4 r;
+                r.x = rn_tf32(v[q].x - __uint_as_float(__float_as_uint(v[q].x) & 0xffffe000u));
+                r.y = rn_tf32(v[q].y - __uint_as_float(__float_as_uint(v[q].y) & 0xffffe000u));
+                r.z = rn_tf32(v[q].z - __uint_as_float(__float_as_uint(v[q].z) & 0xffffe000u));
+                r.w = rn_tf32(v[q].w - __uint_as_float(__float_as_uint(v[q].w) & 0xffffe000u));
+                l4[t + kSplit * q] = r;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&lo_full[lo]);
+            if (++lo == NLO) {
+                lo = 0;
+                lo_phase ^= 1u;
+            }
+            if (++stage == STAGES) {
+                stage = 0;
+                phase ^= 1u;
+            }
+        }
     } else {
-        // ---------------- split (TF32X3) and accumulation: warps 2..9, 256 threads
+        // ---------------- accumulation: warps 6..9 (SR) or 2..9
         // Thread (quad, lane, half) owns row quad*32 + lane of the tile and
         // columns [half*HC, half*HC + HC) of each accumulator region.  Each
         // chunk of DRAIN k blocks is accumulated by the tensor core in one
         // TMEM buffer, then read here and added into FP32 registers with
         // round-to-nearest adds: the tensor core's own accumulation rounds
         // toward zero, which over a long chain biases the sum low.
-        // X3 split: the tensor core reads A through its TF32 conversion,
-        // which truncates, so A itself acts as the high part and the
-        // remainder A - trunc(A), rounded to TF32, is written to the low ring.
-        constexpr int HC = NPAD / 2;                 // columns per thread per region
-        const int t = threadIdx.x - 64;              // 0..255
+        constexpr int HC = SR ? NPAD : NPAD / 2;     // columns per thread per region
         const int quad = warp & 3;                   // TMEM lane quadrant this warp may read
-        const int half = (warp - 2) >> 2;
+        const int half = SR ? 0 : (warp - 2) >> 2;
         const uint32_t lane_base = ((uint32_t)(quad * 32) << 16) + half * HC;
         float acc[HC];
 #pragma unroll
         for (int j = 0; j < HC; ++j)
             acc[j] = 0.f;
-        int stage = 0, buf = 0, pos = 0, pending = -1, lo = 0;
-        uint32_t phase = 0, lo_phase = 0, drains0 = 0, drains1 = 0;
+        int buf = 0, pos = 0, pending = -1;
+        uint32_t drains0 = 0, drains1 = 0;
+        int stage = 0, lo = 0;                       // inline split (X3 without SR)
+        uint32_t phase = 0, lo_phase = 0;
+        const int t = threadIdx.x - 64;
         bool ok = true;
         auto ld_add = [&](uint32_t addr) {
             if constexpr (HC >= 16) {
@@ -414,14 +471,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_arrive(&acc_empty[b]);
             return true;
         };
+        int tile = tile0, kb = kb0 - 1;
         for (int64_t it = it0; it < it1 && ok; ++it) {
-            const int tile = (int)(it / KB), kb = (int)(it % KB);
+            if (++kb == KB) {
+                kb = 0;
+                ++tile;
+            }
             const bool seg_start = it == it0 || kb == 0;
             const bool seg_end = it + 1 == it1 || kb == KB - 1;
             pos = seg_start ? 0 : pos + 1;
             const bool chunk_end = seg_end || pos % DRAIN == DRAIN - 1;
-            if constexpr (X3) {
-                // warp-uniform decisions: every lane of the warp continues or none
+            if constexpr (X3 && !SR) {
+                // split this stage first (same step as the split warps above)
                 if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, deadline, abort_flag)))
                     break;
                 if (!__all_sync(0xffffffffu,
@@ -431,14 +492,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float4 *l4 = reinterpret_cast<float4 *>(LO(lo));
 #pragma unroll
                 for (int q = 0; q < (int)(kABytes / 16 / kEpi); ++q) {
-                    const int idx = t + kEpi * q;
-                    const float4 v = a4[idx];
+                    const float4 v = a4[t + kEpi * q];
                     float4 r;
                     r.x = rn_tf32(v.x - __uint_as_float(__float_as_uint(v.x) & 0xffffe000u));
                     r.y = rn_tf32(v.y - __uint_as_float(__float_as_uint(v.y) & 0xffffe000u));
                     r.z = rn_tf32(v.z - __uint_as_float(__float_as_uint(v.z) & 0xffffe000u));
                     r.w = rn_tf32(v.w - __uint_as_float(__float_as_uint(v.w) & 0xffffe000u));
-                    l4[idx] = r;
+                    l4[t + kEpi * q] = r;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(&lo_full[lo]);
@@ -446,10 +506,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     lo = 0;
                     lo_phase ^= 1u;
                 }
-            }
-            if (++stage == STAGES) {
-                stage = 0;
-                phase ^= 1u;
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
             }
             // drain the previous chunk now that the tensor core has the next one
             if (pending >= 0) {

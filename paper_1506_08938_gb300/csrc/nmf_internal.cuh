@@ -16,6 +16,7 @@ constexpr int kMaxRank = 128;
 // Device status word bits (latched until nmf_sync).
 constexpr unsigned kStNonFinite = 1u;
 constexpr unsigned kStTimeout = 2u;
+constexpr unsigned kStBadInput = 4u;   // an argument in device memory broke its contract
 
 void count_launch(int n = 1);
 
@@ -52,9 +53,11 @@ struct NnlsArgs {
     unsigned long long *iter_total;   // optional sum of counts
     unsigned *s_final_max;  // optional: atomicMax of final ||f||^2 bits
     unsigned *status;       // optional device status word
+    int lanes;              // lanes per row (0: chosen from r)
 };
 cudaError_t launch_nnls(const NnlsArgs &a, cudaStream_t s);
-cudaError_t prepare_nnls(int r);
+cudaError_t prepare_nnls(int r, int lanes);
+bool nnls_layout(int r, int lanes, int *G, int *J);
 
 // ---- Gram / cross term (SIMT FP32) ----------------------------------------
 // partial Gram slices: P[s] = X[k0:k1]^T X[k0:k1], s < nsplit, each r x r.

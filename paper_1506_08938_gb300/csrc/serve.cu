@@ -137,6 +137,7 @@ nmf_status launch_batch(nmf_server_s *S, Slot &sl)
     a.max_inner = S->o.nnls.max_inner;
     a.eps = (float)S->o.nnls.eps;
     a.cd_steps = S->o.nnls.cd_steps;
+    a.lanes = S->o.nnls.lanes;
     if (launch_nnls(a, st) != cudaSuccess)
         return NMF_E_CUDA;
     if (cudaMemcpyAsync(sl.host, H, 4 * (size_t)cols * r, cudaMemcpyDeviceToHost, st) !=
@@ -248,6 +249,13 @@ NMF_API nmf_status nmf_server_create(nmf_server_t *out, int device, const float 
     S->o = *opts;
     if (S->o.nnls.max_inner <= 0)
         nmf_nnls_opts_default(&S->o.nnls);
+    {
+        int lg = 0, lj = 0;
+        if (!nnls_layout(r, S->o.nnls.lanes, &lg, &lj)) {
+            delete S;
+            return NMF_E_ARG;
+        }
+    }
     S->slot_bytes = batch_bytes(opts->max_batch_cols, opts->max_batch_nnz, r);
     S->host_bytes = S->slot_bytes;
     // basis Gram, rescaled once: Qt and d (the E-step's shared Q, Alg. 2)
@@ -263,7 +271,7 @@ NMF_API nmf_status nmf_server_create(nmf_server_t *out, int device, const float 
     if (launch_gram_partial(W, wrows, r, r, P, gs, nullptr) != cudaSuccess ||
         launch_sum_slices(P, gs, (int64_t)r * r, G, nullptr) != cudaSuccess ||
         launch_rescale(G, 1, r, 0.f, nullptr, nullptr, S->Qt, S->d, nullptr) != cudaSuccess ||
-        prepare_nnls(r) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        prepare_nnls(r, S->o.nnls.lanes) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         cudaFree(S->gram_ws);
         delete S;
         return NMF_E_CUDA;

@@ -115,10 +115,16 @@ def test_dense_solve_against_oracle_trajectory(h, dense_inst):
     o = P.solve_opts(T, beta_w=0.1, beta_h=0.1, nnls=P.nnls_opts(max_inner=50, eps=1e-3),
                      objective="direct", obj_hist=hist.ctypes.data_as(C.POINTER(C.c_double)))
     P.nmf_solve(h, t32(inst.V), W, Ht, o)
-    # the trajectory amplifies FP32 rounding (see the regularised-instance
-    # test); over three iterations it stays within 1e-3 of the oracle's
-    rel = np.abs(hist - plain[:T]) / plain[:T]
-    assert rel.max() < 1e-3, rel
+    # With the relative stop rule (eps = 1e-3) a row whose ||P||^2 lands
+    # within rounding of the threshold stops one inner iteration earlier or
+    # later in FP32 than in FP64 (about 2% of rows, cf. the stop-count
+    # parity test); such a row's objective moves by a fraction of what the
+    # whole outer iteration gains.  So each iteration's objective must agree
+    # to 5% of that iteration's decrease on the oracle's trajectory.
+    J0 = O.objective_dense(inst.V, inst.W0, inst.Ht0, 0.0, 0.0, 0.1, 0.1)
+    prev = np.concatenate([[J0], plain[:T - 1]])
+    dev = np.abs(hist - plain[:T])
+    assert np.all(dev <= 0.05 * (prev - plain[:T])), (dev, prev - plain[:T])
 
 
 @pytest.fixture(scope="module")
