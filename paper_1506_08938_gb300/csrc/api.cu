@@ -638,6 +638,7 @@ struct HalfStep {
 
 struct Loop {
     int r;
+    unsigned *ticket;   // last-CTA counter of the factor preparation
     float *Pg;          // Gram partial slices
     int gS_w, gS_h;     // gram splits for W (m rows) and Ht (n rows)
     float *Gw, *Gh;     // Grams without beta
@@ -651,17 +652,43 @@ struct Loop {
     double *obj_partials;
 };
 
-nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, const float *Gother)
+// The factor X just updated feeds the next half-step `next`: its Gram G,
+// next.Q = G + beta I, the rescaled Qt, d (Alg. 3) and the packed operand of
+// next's tensor-core cross term, in one launch.
+nmf_status enqueue_prep(nmf_handle h, Loop &L, const float *X, int64_t rows, float *G,
+                        HalfStep &next)
+{
+    PrepArgs a{};
+    a.X = X;
+    a.rows = rows;
+    a.r = L.r;
+    a.beta = next.beta;
+    a.P = L.Pg;
+    a.ticket = L.ticket;
+    a.G = G;
+    a.Q = next.Q;
+    a.Qt = L.Qt;
+    a.d = L.d;
+    a.pack_mode = next.tc_mode;
+    a.pack = next.pack;
+    if (next.tc_mode >= 0) {
+        a.npad = tc_npad(L.r);
+        a.kp = tc_kpad(rows, next.tc_mode);
+    }
+    CK(launch_factor_prep(a, h->stream));
+    return NMF_OK;
+}
+
+// One half-step once Qt, d and the packed factor are in place: the cross
+// term C = V X_other, then every row's NQP (Alg. 3).
+nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s)
 {
     cudaStream_t st = h->stream;
-    // Q = G_other + beta I; Qt, d (Alg. 3 rescale)
-    CK(launch_rescale(Gother, 1, L.r, s.beta, nullptr, s.Q, L.Qt, L.d, st));
     // cross term C = V X_other
     if (s.sparse) {
         CK(launch_spmm_csr(s.csr->rowptr, s.csr->colidx, s.csr->vals, s.csr->dt, s.csr->rows,
                            s.csr->nnz, s.Xo, L.r, s.Cs, s.spplan, L.spws, st));
     } else if (s.tc_mode >= 0) {
-        CK(launch_tc_pack(s.Xo, s.K, L.r, s.tc_mode, s.pack, st));
         CK(launch_tc_cross(s.Atc, s.rows, s.K, s.lda_tc, L.r, s.tc_mode, s.pack, s.Cs, s.plan,
                            h->status, st));
     } else {
@@ -696,17 +723,19 @@ nmf_status enqueue_objective(nmf_handle h, Loop &L, const nmf_solve_opts &o, dou
 
 nmf_status enqueue_iteration(nmf_handle h, Loop &L, const nmf_solve_opts &o)
 {
+    (void)o;
     nmf_status s;
-    // W-update (E-step): Q_W = Ht^T Ht + b_w I (G_H ready), C_W = V Ht
-    if ((s = enqueue_half(h, L, L.hw, L.Gh)))
+    // W-update (E-step): C_W = V Ht against Q_W = Ht^T Ht + b_w I, ready
+    if ((s = enqueue_half(h, L, L.hw)))
         return s;
-    // G_W = W^T W
-    if ((s = gram_into(h, L.hw.X, L.hw.rows, L.r, L.r, o.prec, L.Pg, L.gS_w, L.Gw)))
+    // G_W = W^T W -> Q_H, Qt, d and packed W for the H-update
+    if ((s = enqueue_prep(h, L, L.hw.X, L.hw.rows, L.Gw, L.hh)))
         return s;
     // H-update (M-step)
-    if ((s = enqueue_half(h, L, L.hh, L.Gw)))
+    if ((s = enqueue_half(h, L, L.hh)))
         return s;
-    if ((s = gram_into(h, L.hh.X, L.hh.rows, L.r, L.r, o.prec, L.Pg, L.gS_h, L.Gh)))
+    // G_H = Ht^T Ht -> Q_W, Qt, d and packed Ht for the next W-update
+    if ((s = enqueue_prep(h, L, L.hh.X, L.hh.rows, L.Gh, L.hw)))
         return s;
     return NMF_OK;
 }
@@ -928,7 +957,11 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     // ---- workspace layout
     L.gS_w = gram_splits(m);
     L.gS_h = gram_splits(n);
-    const int gS = L.gS_w > L.gS_h ? L.gS_w : L.gS_h;
+    int gS = L.gS_w > L.gS_h ? L.gS_w : L.gS_h;
+    {
+        const int ps = prep_slices(m > n ? m : n);
+        gS = ps > gS ? ps : gS;
+    }
     int sw = 1, sh = 1;
     SpmmPlan pw{}, ph{};
     if (sparse) {
@@ -971,6 +1004,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     Sizer z;
     z.add<double>(n_objp);
     z.add<float>((size_t)gS * r * r);
+    z.add<unsigned>(4);
     z.add<float>((size_t)r * r);
     z.add<float>((size_t)r * r);
     z.add<float>((size_t)r * r);
@@ -996,6 +1030,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
         L.ldv = V->d.ld;
     }
     L.Pg = a.take<float>((size_t)gS * r * r);
+    L.ticket = a.take<unsigned>(4);
     L.Gw = a.take<float>((size_t)r * r);
     L.Gh = a.take<float>((size_t)r * r);
     L.Qt = a.take<float>((size_t)r * r);
@@ -1087,6 +1122,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
         return NMF_E_NOTIMPL;   // strided dense V: pass a contiguous V
     CK(cudaMemsetAsync(h->ctr, 0, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(h->idev, 0, 2 * sizeof(int), s));
+    CK(cudaMemsetAsync(L.ticket, 0, 4 * sizeof(unsigned), s));
     CK(cudaMemcpyAsync(&L.vv, vv_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
 
@@ -1094,8 +1130,8 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, s));
-    // G_H = Ht^T Ht for the first W-update
-    st = gram_into(h, Ht, n, r, r, o.prec, L.Pg, L.gS_h, L.Gh);
+    // G_H = Ht^T Ht, Q_W, Qt, d and packed Ht for the first W-update
+    st = enqueue_prep(h, L, Ht, n, L.Gh, hw);
     if (st)
         return st;
 

@@ -1,0 +1,218 @@
+// Factor preparation between two half-steps: the factor X just updated
+// (rows x r) yields
+//   * G = X^T X                  (Gram of Alg. 2, FP32; kept for the objective)
+//   * Q = G + beta I             (kept for the KKT check)
+//   * Qt = D^-1/2 Q D^-1/2, d    (the rescaled problem of Alg. 3, §3.4)
+//   * the packed operand of the next tensor-core cross term (optional).
+// Two launches replace four (Gram partials, slice sum, rescale, packing):
+//   1. CTAs over row ranges of 32+ rows accumulate Gram partials in registers
+//      and write their columns of the packed factor;
+//   2. CTAs over 32-element column groups of G sum the partials - 16 warps
+//      over interleaved slices, then the warp sums in warp order: a fixed
+//      order, so the result is reproducible - and the last CTA to finish
+//      (ticket counter) rescales and clears the counter.
+#include "nmf_internal.cuh"
+
+namespace nmfi {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRowsBlock = 32;     // rows staged in shared memory at a time
+constexpr int kMaxSlices = 512;    // Gram partials at most
+constexpr int kSumWarps = 16;      // warps of a reduction CTA
+
+// nearest TF32 value (10-bit mantissa)
+__device__ __forceinline__ float rn_tf32(float v)
+{
+    return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xffffe000u);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kThreads) k_factor_prep(const PrepArgs a)
+{
+    constexpr int T = NB / 16;
+    __shared__ float Xs[kRowsBlock][NB + 1];
+    const int r = a.r, tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+    const int64_t k0 = (int64_t)blockIdx.x * a.chunk;
+    const int64_t k1 = k0 + a.chunk < a.rows ? k0 + a.chunk : a.rows;
+    float acc[T][T];
+#pragma unroll
+    for (int i = 0; i < T; ++i)
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+            acc[i][j] = 0.f;
+
+    for (int64_t kb = k0; kb < k1; kb += kRowsBlock) {
+        for (int idx = tid; idx < kRowsBlock * NB; idx += kThreads) {
+            const int kk = idx / NB, c = idx - kk * NB;
+            const int64_t gk = kb + kk;
+            Xs[kk][c] = (c < r && gk < k1) ? a.X[gk * r + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kRowsBlock; ++kk) {
+            float xa[T], xb[T];
+#pragma unroll
+            for (int i = 0; i < T; ++i)
+                xa[i] = Xs[kk][ti + 16 * i];
+#pragma unroll
+            for (int j = 0; j < T; ++j)
+                xb[j] = Xs[kk][tj + 16 * j];
+#pragma unroll
+            for (int i = 0; i < T; ++i)
+#pragma unroll
+                for (int j = 0; j < T; ++j)
+                    acc[i][j] = fmaf(xa[i], xb[j], acc[i][j]);
+        }
+        // packed operand: row n of the pack holds column n of X along k
+        if (a.pack_mode >= 0) {
+            for (int idx = tid; idx < a.npad * kRowsBlock; idx += kThreads) {
+                const int n = idx / kRowsBlock, kk = idx - n * kRowsBlock;
+                const int64_t gk = kb + kk;
+                if (gk >= k1)
+                    continue;
+                const float v = Xs[kk][n];   // zero for n >= r
+                const int64_t o = (int64_t)n * a.kp + gk;
+                if (a.pack_mode == TC_BF16) {
+                    reinterpret_cast<__nv_bfloat16 *>(a.pack)[o] = __float2bfloat16_rn(v);
+                } else if (a.pack_mode == TC_TF32X3) {
+                    const float hi = rn_tf32(v);
+                    reinterpret_cast<float *>(a.pack)[o] = hi;
+                    reinterpret_cast<float *>(a.pack)[(int64_t)a.npad * a.kp + o] =
+                        rn_tf32(v - hi);
+                } else {
+                    reinterpret_cast<float *>(a.pack)[o] = v;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    float *Ps = a.P + (int64_t)blockIdx.x * r * r;
+#pragma unroll
+    for (int i = 0; i < T; ++i)
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+            const int ii = ti + 16 * i, jj = tj + 16 * j;
+            if (ii < r && jj < r)
+                Ps[ii * r + jj] = acc[i][j];
+        }
+}
+
+// G[e] = sum_s P[s][e] for 32 consecutive e per CTA, then (last CTA) Q, Qt, d
+__global__ void __launch_bounds__(kSumWarps * 32) k_prep_finish(const PrepArgs a, int S)
+{
+    __shared__ float part[kSumWarps][33];
+    __shared__ float sd[kMaxRank];
+    __shared__ int last;
+    const int r = a.r, n = r * r;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        if (e < n) {
+            int k = w;
+            for (; k + 3 * kSumWarps < S; k += 4 * kSumWarps) {
+                s0 += a.P[(int64_t)k * n + e];
+                s1 += a.P[(int64_t)(k + kSumWarps) * n + e];
+                s2 += a.P[(int64_t)(k + 2 * kSumWarps) * n + e];
+                s3 += a.P[(int64_t)(k + 3 * kSumWarps) * n + e];
+            }
+            for (; k < S; k += kSumWarps)
+                s0 += a.P[(int64_t)k * n + e];
+        }
+        part[w][lane] = (s0 + s1) + (s2 + s3);
+    }
+    __syncthreads();
+    if (w == 0 && e < n) {
+        float s = 0.f;
+#pragma unroll
+        for (int q = 0; q < kSumWarps; ++q)
+            s += part[q][lane];
+        a.G[e] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last)
+        return;
+    __threadfence();
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+        const float qii = a.G[i * r + i] + a.beta;
+        sd[i] = qii > 0.f ? sqrtf(qii) : 0.f;
+        a.d[i] = qii > 0.f ? sd[i] : 1.f;
+    }
+    __syncthreads();
+    for (int f = threadIdx.x; f < n; f += blockDim.x) {
+        const int i = f / r, j = f - i * r;
+        const float g = a.G[f];
+        const float q = i == j ? g + a.beta : g;
+        if (a.Q)
+            a.Q[f] = q;
+        float v;
+        if (sd[i] == 0.f || sd[j] == 0.f)
+            v = 0.f;   // dead coordinate (Q_ii <= 0): held at 0
+        else if (i == j)
+            v = 1.f;
+        else
+            v = q / (sd[i] * sd[j]);
+        a.Qt[f] = v;
+    }
+    // zero columns K .. kp-1 of the pack (k padding of the last k block)
+    if (a.pack_mode >= 0) {
+        const int64_t padk = a.kp - a.rows;
+        for (int64_t idx = threadIdx.x; idx < (int64_t)a.npad * padk; idx += blockDim.x) {
+            const int64_t nn = idx / padk, o = nn * a.kp + a.rows + (idx - nn * padk);
+            if (a.pack_mode == TC_BF16) {
+                reinterpret_cast<__nv_bfloat16 *>(a.pack)[o] = __float2bfloat16_rn(0.f);
+            } else {
+                reinterpret_cast<float *>(a.pack)[o] = 0.f;
+                if (a.pack_mode == TC_TF32X3)
+                    reinterpret_cast<float *>(a.pack)[(int64_t)a.npad * a.kp + o] = 0.f;
+            }
+        }
+    }
+    if (threadIdx.x == 0)
+        *a.ticket = 0u;   // ready for the next launch (graph replays included)
+}
+
+}  // namespace
+
+// rows per CTA: 32, more only to keep the partials within kMaxSlices
+int64_t prep_chunk(int64_t rows)
+{
+    int64_t c = (rows + kMaxSlices - 1) / kMaxSlices;
+    c = c < kRowsBlock ? kRowsBlock : c;
+    return (c + kRowsBlock - 1) / kRowsBlock * kRowsBlock;
+}
+
+int prep_slices(int64_t rows)
+{
+    const int64_t c = prep_chunk(rows);
+    const int64_t s = (rows + c - 1) / c;
+    return s < 1 ? 1 : (int)s;
+}
+
+cudaError_t launch_factor_prep(const PrepArgs &a0, cudaStream_t s)
+{
+    ProfScope prof_(KC_GRAM, s);
+    PrepArgs a = a0;
+    if (a.rows <= 0 || a.r < 1 || a.r > kMaxRank || !a.G)
+        return cudaErrorInvalidValue;
+    a.chunk = prep_chunk(a.rows);
+    const int S = prep_slices(a.rows);
+    if (a.r <= 32)
+        k_factor_prep<32><<<S, kThreads, 0, s>>>(a);
+    else if (a.r <= 64)
+        k_factor_prep<64><<<S, kThreads, 0, s>>>(a);
+    else
+        k_factor_prep<128><<<S, kThreads, 0, s>>>(a);
+    count_launch();
+    const int n = a.r * a.r;
+    k_prep_finish<<<(n + 31) / 32, kSumWarps * 32, 0, s>>>(a, S);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace nmfi

@@ -59,6 +59,25 @@ cudaError_t launch_nnls(const NnlsArgs &a, cudaStream_t s);
 cudaError_t prepare_nnls(int r, int lanes);
 bool nnls_layout(int r, int lanes, int *G, int *J);
 
+// ---- factor preparation (Gram + rescale + tensor-core packing, one launch) --
+struct PrepArgs {
+    const float *X;         // factor just updated, rows x r (row-major, ld = r)
+    int64_t rows;
+    int r;
+    float beta;             // L2 weight of the next half-step
+    float *P;               // partial Gram slices (prep_slices(rows) x r x r)
+    unsigned *ticket;       // zero before the first launch; left zero
+    float *G, *Q;           // optional: X^T X and X^T X + beta I
+    float *Qt, *d;          // rescaled Q and its scale
+    int pack_mode;          // -1: no packing; else a TcMode
+    void *pack;             // packed operand (npad x kp), X3: hi rows then lo rows
+    int npad;
+    int64_t kp;
+    int64_t chunk;          // rows per CTA (set by the launcher)
+};
+cudaError_t launch_factor_prep(const PrepArgs &a, cudaStream_t s);
+int prep_slices(int64_t rows);
+
 // ---- Gram / cross term (SIMT FP32) ----------------------------------------
 // partial Gram slices: P[s] = X[k0:k1]^T X[k0:k1], s < nsplit, each r x r.
 cudaError_t launch_gram_partial(const float *X, int64_t rows, int64_t ld, int r, float *P,
