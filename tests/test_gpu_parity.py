@@ -507,3 +507,19 @@ def test_zero_rows_and_bad_rank(h):
     h.sync()
     with pytest.raises(P.NmfError):
         P.nmf_rescale(h, t32(np.eye(129)))
+
+
+def test_sharded_schedule_single_rank_on_gpu(h):
+    """The multi-GPU schedule's device ops (one rank, no collective) give one
+    outer iteration within the per-step FP32 bounds of the oracle's."""
+    from paper_1506_08938_gb300.sharded import GpuOps, ShardOpts, sharded_iteration
+    inst = f32_inst(WL.tiny(seed=2, r=10))
+    K = 3
+    ops = GpuOps(h, P.nnls_opts(max_inner=K, eps=0.0))
+    V = t32(inst.V)
+    W, Ht = sharded_iteration(V, V.t().contiguous(), t32(inst.W0), t32(inst.Ht0), ops,
+                              ShardOpts())
+    Wo, Ho, _, _ = O.nmf_solve(inst.W0, inst.Ht0, 1, V=inst.V, opts=O.nqp_opts(max_inner=K, eps=0.0))
+    tw, th = step_bounds(Wo, inst.Ht0, 10)
+    assert rel_err(to_np(W), Wo) < tw
+    assert rel_err(to_np(Ht), Ho) < th
