@@ -264,6 +264,13 @@ typedef struct {
 nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance *inst,
                              const nmf_solve_opts *opts, int mode, nmf_report *reps);
 
+/* ---- diagnostics ------------------------------------------------------------ */
+
+/* FP32 FFMA throughput of the current device in TFLOP/s (*tflops, host),
+ * measured with independent fmaf chains on every SM: the ALU roofline of
+ * the CUDA-core kernels.  Synchronises the device; allocates a few bytes. */
+nmf_status nmf_peak_fp32(double *tflops);
+
 /* ---- projection onto a fixed basis ----------------------------------------- */
 
 /* E-step alone (Alg. 1 E-step, Alg. 2 first loop) against a fixed basis W

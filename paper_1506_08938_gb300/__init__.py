@@ -123,12 +123,20 @@ def _load():
     L.nmf_server_wait.argtypes = [_P, C.c_int64, C.c_double, C.POINTER(C.c_double)]
     L.nmf_server_stats.argtypes = [_P, C.POINTER(ServerStats)]
     L.nmf_server_destroy.argtypes = [_P]
+    L.nmf_peak_fp32.argtypes = [C.POINTER(C.c_double)]
     L.nmf_profile_enable.argtypes = [C.c_int]
     L.nmf_profile_read.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     return L
 
 
 KCLASS = {"gram": 0, "cross": 1, "spmm": 2, "rescale": 3, "nnls": 4, "objective": 5, "other": 6}
+
+
+def nmf_peak_fp32() -> float:
+    """Measured FP32 FFMA throughput of the current device, TFLOP/s."""
+    v = C.c_double(0.0)
+    _check(lib().nmf_peak_fp32(C.byref(v)), "nmf_peak_fp32")
+    return v.value
 
 
 def nmf_profile_enable(enable: bool = True):

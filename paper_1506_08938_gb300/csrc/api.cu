@@ -1517,6 +1517,14 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
     return nmf_sync(h);
 }
 
+NMF_API nmf_status nmf_peak_fp32(double *tflops)
+{
+    if (!tflops)
+        return NMF_E_ARG;
+    CK(measure_fp32_peak(tflops));
+    return NMF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // projection onto a fixed basis
 // ---------------------------------------------------------------------------

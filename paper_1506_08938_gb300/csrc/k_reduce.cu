@@ -447,3 +447,67 @@ cudaError_t launch_f32_to_bf16(const float *x, int64_t n, __nv_bfloat16 *y, cuda
 }
 
 }  // namespace nmfi
+
+// ---- FP32 FFMA throughput probe ---------------------------------------------
+// Eight independent dependent chains of fmaf per thread, enough warps per SM
+// to keep every FMA lane busy; the result is stored only if it equals a value
+// the chains never reach, so the compiler keeps the work.
+namespace nmfi {
+namespace {
+__global__ void __launch_bounds__(256) k_ffma_probe(float *out, int iters, float seed)
+{
+    float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        a[j] = seed + 1e-3f * (float)(threadIdx.x + j);
+    const float mlt = 0.9999999f, add = 1e-7f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            a[j] = fmaf(a[j], mlt, add);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        s += a[j];
+    if (s == -1.0f)
+        out[blockIdx.x] = s;
+}
+}  // namespace
+
+cudaError_t measure_fp32_peak(double *tflops)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ffma_probe, 256, 0);
+    if (e != cudaSuccess)
+        return e;
+    const int grid = sms * (per_sm > 0 ? per_sm : 1);
+    const int iters = 8192;
+    float *out = nullptr;
+    if ((e = cudaMalloc(&out, sizeof(float) * grid)) != cudaSuccess)
+        return e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_ffma_probe<<<grid, 256>>>(out, iters, 1.f);   // warm-up (clocks ramp)
+    k_ffma_probe<<<grid, 256>>>(out, iters, 1.f);
+    cudaEventRecord(e0);
+    const int reps = 5;
+    for (int i = 0; i < reps; ++i)
+        k_ffma_probe<<<grid, 256>>>(out, iters, 1.f);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess)
+        return e;
+    const double flops = 2.0 * 8.0 * iters * 256.0 * grid * reps;
+    *tflops = flops / (ms * 1e-3) / 1e12;
+    return cudaGetLastError();
+}
+}  // namespace nmfi

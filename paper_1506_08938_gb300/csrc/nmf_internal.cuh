@@ -59,6 +59,9 @@ cudaError_t launch_nnls(const NnlsArgs &a, cudaStream_t s);
 cudaError_t prepare_nnls(int r, int lanes);
 bool nnls_layout(int r, int lanes, int *G, int *J);
 
+// FP32 FFMA throughput of this GPU, measured (TFLOP/s)
+cudaError_t measure_fp32_peak(double *tflops);
+
 // ---- factor preparation (Gram + rescale + tensor-core packing, one launch) --
 struct PrepArgs {
     const float *X;         // factor just updated, rows x r (row-major, ld = r)
