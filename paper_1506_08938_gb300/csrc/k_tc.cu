@@ -38,7 +38,8 @@
 namespace nmfi {
 namespace {
 
-constexpr int kThreads = 320;     // producer, MMA, 8 split/accumulate warps
+constexpr int kThreads = 384;     // producer, up to 3 MMA issuers, 8 split/accumulate warps
+constexpr int kIssuer0 = 1, kIssuer1 = 10, kIssuer2 = 11;   // warps that issue tcgen05.mma
 constexpr int kEpi = 256;         // threads of warps 2..9
 constexpr int kSplit = 128;       // TF32X3: warps 2..5 split, warps 6..9 accumulate
 constexpr uint32_t kABytes = 128 * 128;   // 128 rows x 128 bytes
@@ -101,6 +102,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity,
                 return false;
             }
         }
+    }
+}
+
+// Wait during teardown: only the deadline ends it (the abort flag is already
+// set), so copies and MMAs this CTA issued land before it exits.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t *b, uint32_t parity,
+                                                unsigned long long deadline)
+{
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try(b, parity))
+            return true;
+        if ((i & 63) == 63 && gtimer() > deadline)
+            return false;
     }
 }
 
@@ -222,7 +236,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int KSTEP_ELEMS = MODE == TC_BF16 ? 64 : 32;   // elements per 128-byte row
     constexpr int KMMA = 4;                                   // MMAs of 32 bytes per stage
     constexpr uint32_t BUF_COLS = NB <= 32 ? 32 : (NB <= 64 ? 64 : (NB <= 128 ? 128 : 256));
-    constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;   // two accumulators
+    // MMA issuers and accumulator buffers: each issuer owns every NISS-th
+    // buffer, so the accumulating warps may lag the tensor core by several
+    // chunks; three issuers where three buffers fit in TMEM's 512 columns
+    constexpr int NISS = 512 / BUF_COLS >= 3 ? 3 : 2;
+    constexpr int NACC = NISS == 3 ? 3 : 2;
+    constexpr uint32_t TMEM_USED = NACC * BUF_COLS;
+    constexpr uint32_t TMEM_COLS = TMEM_USED <= 32 ? 32 : TMEM_USED <= 64 ? 64 :
+                                   TMEM_USED <= 128 ? 128 : TMEM_USED <= 256 ? 256 : 512;
     constexpr uint32_t ID_B = idesc(MODE == TC_BF16 ? 1u : 2u, 128, NB);     // A x packed tile
     constexpr uint32_t ID_HI = idesc(2u, 128, NPAD);                         // A_lo x B_hi
 
@@ -235,8 +256,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES + NLO * kABytes);
     uint64_t *full = bars, *empty = bars + STAGES;
     uint64_t *lo_full = bars + 2 * STAGES, *lo_empty = lo_full + (NLO > 0 ? NLO : 1);
-    uint64_t *acc_full = lo_empty + (NLO > 0 ? NLO : 1), *acc_empty = acc_full + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    uint64_t *acc_full = lo_empty + (NLO > 0 ? NLO : 1), *acc_empty = acc_full + NACC;
+    uint64_t *fin = acc_empty + NACC;   // every MMA of issuer q has completed: fin[q]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 3);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -257,7 +279,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&lo_full[j], SPLIT_T);
             mbar_init(&lo_empty[j], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int q = 0; q < 3; ++q)
+            mbar_init(&fin[q], 1);
+        for (int b = 0; b < NACC; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], SR ? kEpi - kSplit : kEpi);
         }
@@ -302,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int s = 0; s < STAGES; ++s) {
                 if (!mbar_wait(&empty[stage], phase ^ 1u, deadline + kDeadlineNs, abort_flag)) {
                     // the consumer stopped; wait for the load itself instead
-                    mbar_wait(&full[stage], phase, deadline + 2 * kDeadlineNs, abort_flag);
+                    mbar_wait_drain(&full[stage], phase, deadline + 2 * kDeadlineNs);
                 }
                 if (++stage == STAGES) {
                     stage = 0;
@@ -310,11 +334,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer
-        if (lane == 0) {
-            int stage = 0, buf = 0, pos = 0, lo = 0;
-            uint32_t phase = 0, lo_phase = 0, uses0 = 0, uses1 = 0;
+    } else if (warp == kIssuer0 || warp == kIssuer1 || warp == kIssuer2) {
+        // ---------------- MMA issuers: issuer q takes the accumulation chunks
+        // c with c % NISS == q, so one thread's barrier waits and commits
+        // overlap the others' MMAs.  Chunk c accumulates in buffer c % NACC
+        // (NACC == NISS), which only its issuer touches; stage and low-part
+        // reuse stay ordered through the producer and split barriers, and
+        // tcgen05.commit tracks the MMAs of the thread that issues it.
+        const int q = warp == kIssuer0 ? 0 : (warp == kIssuer1 ? 1 : 2);
+        if (lane == 0 && q < NISS) {
+            int stage = 0, buf = 0, pos = 0, lo = 0, chunk = -1;
+            uint32_t phase = 0, lo_phase = 0, uses[NACC] = {};
             int kb = kb0 - 1;
             for (int64_t it = it0; it < it1; ++it) {
                 if (++kb == KB)
@@ -324,53 +354,58 @@ __global__ void __launch_bounds__(kThreads, 1)
                 pos = seg_start ? 0 : pos + 1;
                 const bool chunk_start = pos % DRAIN == 0;
                 const bool chunk_end = seg_end || pos % DRAIN == DRAIN - 1;
-                if (chunk_start) {
-                    // the accumulating warps have drained the previous use of this buffer
-                    const uint32_t u = buf ? uses1 : uses0;
-                    if (!mbar_wait(&acc_empty[buf], (u & 1u) ^ 1u, deadline, abort_flag))
-                        break;
-                    if (buf)
-                        ++uses1;
-                    else
-                        ++uses0;
-                    tc_fence_after();
-                }
-                if (!mbar_wait(&full[stage], phase, deadline, abort_flag))
-                    break;
-                if constexpr (X3) {
-                    if (!mbar_wait(&lo_full[lo], lo_phase, deadline, abort_flag))
-                        break;
-                }
-                tc_fence_after();
-                const uint32_t d = tmem + buf * BUF_COLS;
-                const uint32_t a0 = su32(A(stage)), b0 = su32(B(stage));
-#pragma unroll
-                for (int kk = 0; kk < KMMA; ++kk) {
-                    const uint64_t ad = sdesc(a0 + 32 * kk), bd = sdesc(b0 + 32 * kk);
-                    // X3: columns [0, NPAD) get A B_hi, columns [NPAD, 2 NPAD) get A B_lo
-                    mma<MODE>(d, ad, bd, ID_B, (chunk_start && kk == 0) ? 0u : 1u);
-                    if constexpr (X3) {
-                        const uint64_t adl = sdesc(su32(LO(lo)) + 32 * kk);
-                        mma<MODE>(d, adl, bd, ID_HI, 1u);   // A_lo x B_hi (first NPAD rows)
+                if (chunk_start)
+                    ++chunk;
+                if (chunk % NISS == q) {
+                    if (chunk_start) {
+                        // the accumulating warps have drained the previous use of this buffer
+                        const uint32_t u = uses[buf]++;
+                        if (!mbar_wait(&acc_empty[buf], (u & 1u) ^ 1u, deadline, abort_flag))
+                            break;
+                        tc_fence_after();
                     }
+                    if (!mbar_wait(&full[stage], phase, deadline, abort_flag))
+                        break;
+                    tc_fence_after();
+                    const uint32_t d = tmem + buf * BUF_COLS;
+                    const uint32_t a0 = su32(A(stage)), b0 = su32(B(stage));
+                    // X3: columns [0, NPAD) get A B_hi, columns [NPAD, 2 NPAD) get
+                    // A B_lo; these need no low part, so they run while the split finishes
+#pragma unroll
+                    for (int kk = 0; kk < KMMA; ++kk)
+                        mma<MODE>(d, sdesc(a0 + 32 * kk), sdesc(b0 + 32 * kk), ID_B,
+                                  (chunk_start && kk == 0) ? 0u : 1u);
+                    if constexpr (X3) {
+                        if (!mbar_wait(&lo_full[lo], lo_phase, deadline, abort_flag))
+                            break;   // the final commit below waits for the MMAs issued
+                        tc_fence_after();
+                        const uint32_t l0 = su32(LO(lo));
+#pragma unroll
+                        for (int kk = 0; kk < KMMA; ++kk)   // A_lo x B_hi (first NPAD rows)
+                            mma<MODE>(d, sdesc(l0 + 32 * kk), sdesc(b0 + 32 * kk), ID_HI, 1u);
+                        mma_commit(&lo_empty[lo]);
+                    }
+                    mma_commit(&empty[stage]);
+                    if (chunk_end)
+                        mma_commit(&acc_full[buf]);
                 }
-                mma_commit(&empty[stage]);
+                // every issuer walks every k block's ring positions
                 if constexpr (X3) {
-                    mma_commit(&lo_empty[lo]);
                     if (++lo == NLO) {
                         lo = 0;
                         lo_phase ^= 1u;
                     }
                 }
-                if (chunk_end) {
-                    mma_commit(&acc_full[buf]);
-                    buf ^= 1;
-                }
+                if (chunk_end && ++buf == NACC)
+                    buf = 0;
                 if (++stage == STAGES) {
                     stage = 0;
                     phase ^= 1u;
                 }
             }
+            // however the loop ended, no MMA may still write TMEM when it is freed
+            mma_commit(&fin[q]);
+            mbar_wait_drain(&fin[q], 0, deadline + 3 * kDeadlineNs);
         }
     } else if (SR && warp < 6) {
         // ---------------- TF32X3 split: warps 2..5, 128 threads.  The tensor
@@ -431,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < HC; ++j)
             acc[j] = 0.f;
         int buf = 0, pos = 0, pending = -1;
-        uint32_t drains0 = 0, drains1 = 0;
+        uint32_t drains[NACC] = {};
         int stage = 0, lo = 0;                       // inline split (X3 without SR)
         uint32_t phase = 0, lo_phase = 0;
         const int t = threadIdx.x - 64;
@@ -455,13 +490,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         };
         auto drain = [&](int b) -> bool {
-            const uint32_t n = b ? drains1 : drains0;
+            const uint32_t n = drains[b];
             if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], n & 1u, deadline, abort_flag)))
                 return false;
-            if (b)
-                ++drains1;
-            else
-                ++drains0;
+            ++drains[b];
             __syncwarp();
             tc_fence_after();
             ld_add(tmem + b * BUF_COLS + lane_base);
@@ -521,7 +553,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!chunk_end)
                 continue;
             const int b = buf;
-            buf ^= 1;
+            if (++buf == NACC)
+                buf = 0;
             if (!seg_end) {
                 pending = b;
                 continue;
@@ -640,13 +673,14 @@ bool make_map(CUtensorMap *m, const void *base, bool bf16, uint64_t inner, uint6
 
 template <int MODE, int NPAD>
 struct TcCfg {
-    static constexpr int NLO = MODE == TC_TF32X3 ? 2 : 0;       // low-part ring
+    static constexpr int NLO = MODE == TC_TF32X3 ? 3 : 0;       // low-part ring
     static constexpr int NB = MODE == TC_TF32X3 ? 2 * NPAD : NPAD;
     static constexpr int STAGE = kABytes + NB * 128;
-    static constexpr int ST0 = (200 * 1024 - NLO * (int)kABytes) / STAGE;
+    static constexpr int ST0 = (220 * 1024 - NLO * (int)kABytes) / STAGE;
     static constexpr int STAGES = ST0 > 8 ? 8 : ST0;
     static constexpr int DRAIN = MODE == TC_TF32X3 ? 1 : 2;     // k blocks per chunk
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE + (size_t)NLO * kABytes + 1024 + 256;
+    // + 1024 for the 1024-byte alignment of the tiles, + 512 for the barriers
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE + (size_t)NLO * kABytes + 1024 + 512;
 };
 
 template <int MODE, int NPAD>
