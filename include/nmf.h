@@ -257,7 +257,9 @@ typedef struct {
  *          phase (the baseline);
  *  mode 2: as mode 0, with the first iterations spent timing candidate
  *          launch shapes (CTAs per SM, NNLS rows per work item) and the
- *          fastest kept for the rest.
+ *          fastest kept for the rest;
+ *  mode 3: one ordinary launch per phase over all instances (eight per
+ *          outer iteration; no cooperative launch, no grid barrier).
  * reps (host, `count` entries, optional) receive each instance's final J
  * (FP64 element-wise objective), iterations and, in every entry, the batch's
  * device time and mean inner iterations.  Synchronises before returning. */

@@ -395,7 +395,7 @@ def nmf_solve(h: Handle, V, W, Ht, opts: SolveOpts, Vt=None, csr_parts=None, csr
     return rep
 
 
-_BATCH_MODES = {"persistent": 0, "loop": 1, "autotune": 2}
+_BATCH_MODES = {"persistent": 0, "loop": 1, "autotune": 2, "phases": 3}
 
 
 def nmf_solve_batched(h: Handle, instances, opts: SolveOpts, mode="persistent"):
@@ -403,7 +403,8 @@ def nmf_solve_batched(h: Handle, instances, opts: SolveOpts, mode="persistent"):
     tensors (V m x n, Vt its n x m transpose, W m x r, Ht n x r, r <= 64), by
     opts.outer_iters outer iterations, in place.  mode: "persistent" (one
     cooperative launch per iteration for all instances), "loop" (launches per
-    instance and phase) or "autotune".  Returns one Report per instance."""
+    instance and phase), "autotune", or "phases" (one launch per phase over
+    all instances).  Returns one Report per instance."""
     arr = (Instance * len(instances))()
     for k, (V, Vt, W, Ht) in enumerate(instances):
         _need_cuda(V, Vt, W, Ht)

@@ -1286,7 +1286,7 @@ nmf_status batch_offsets(std::vector<int64_t> &hoff, const nmf_instance *inst, i
         int64_t acc = 0;
         for (int i = 0; i < count; ++i) {
             hoff[(size_t)ph * (count + 1) + i] = acc;
-            acc += batched_items(ph, inst[i].m, inst[i].n, nnls_rows);
+            acc += batched_items(ph, inst[i].m, inst[i].n, inst[i].r, nnls_rows);
         }
         hoff[(size_t)ph * (count + 1) + count] = acc;
     }
@@ -1298,7 +1298,7 @@ nmf_status batch_offsets(std::vector<int64_t> &hoff, const nmf_instance *inst, i
 NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance *inst,
                                      const nmf_solve_opts *opts, int mode, nmf_report *reps)
 {
-    if (!h || !inst || !opts || count < 1 || mode < 0 || mode > 2)
+    if (!h || !inst || !opts || count < 1 || mode < 0 || mode > 3)
         return NMF_E_ARG;
     if (opts->outer_iters < 0)
         return NMF_E_ARG;
@@ -1378,7 +1378,7 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
         CK(cudaStreamSynchronize(s));   // hoff is reused
         return NMF_OK;
     };
-    if ((st = set_rows(32)))
+    if ((st = set_rows(1)))
         return st;
     const int max_grid = batched_grid(true);
     int dev = 0, sms = 1;
@@ -1402,8 +1402,8 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
         // autotune: each candidate runs one real outer iteration, timed
         const int per_sm_max = std::max(1, max_grid / sms);
         float best = 1e30f;
-        int best_grid = max_grid, best_rows = 32;
-        const int rows_c[3] = {16, 32, 64};
+        int best_grid = max_grid, best_rows = 1;
+        const int rows_c[3] = {1, 2, 4};   // rows per group of each warp in an NQP item
         for (int ri = 0; ri < 3 && t < opts->outer_iters; ++ri) {
             if ((st = set_rows(rows_c[ri])))
                 return st;
@@ -1470,6 +1470,16 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
         }
         if (gexec)
             cudaGraphExecDestroy(gexec);
+    } else if (mode == 3) {
+        // one launch per phase over all instances: stream order separates
+        // the phases, no grid barrier
+        ba.inst_begin = -1;
+        for (; t < opts->outer_iters; ++t)
+            for (int ph = 0; ph < 8; ++ph) {
+                ba.phase_begin = ph;
+                ba.phase_end = ph + 1;
+                CK(launch_batched(ba, grid, false, s));
+            }
     } else {
         for (; t < opts->outer_iters; ++t)
             for (int ph = 0; ph < 8; ++ph)

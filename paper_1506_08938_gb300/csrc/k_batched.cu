@@ -16,7 +16,9 @@
 // limit).  Loop mode: the same phase code launched once per instance and
 // phase, the baseline whose launch count the persistent form removes.
 // Arithmetic is FP32 on CUDA cores; instance ranks r <= 64.
-#include "nmf_internal.cuh"
+#include <algorithm>
+
+#include "k_nnls.cuh"
 
 namespace nmfi {
 namespace {
@@ -24,7 +26,7 @@ namespace {
 constexpr int kT = 256;            // threads per CTA
 constexpr int kWarps = kT / 32;
 constexpr int kGramRows = 256;     // rows of X per Gram item
-constexpr int kCrossRows = 64;     // rows of A per cross item
+constexpr int kCrossRows = 128;    // rows of A per cross item
 constexpr unsigned long long kBarrierNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned long long gtime()
@@ -173,233 +175,122 @@ __device__ void rescale_item(const float *P, int nparts, int r, float beta, floa
     }
 }
 
-// cross term rows [m0, m0 + kCrossRows) of C = A B (A M x K row-major, B K x r)
+// cross term rows [m0, m0 + kCrossRows) of C = A B (A M x K row-major, B K x r,
+// r <= NB).  Thread (ty, tx) owns rows ty*TM .. ty*TM+TM-1 and columns
+// tx*4 .. tx*4+3; per k a 128-bit load of B and TM loads of A feed 4 TM FMAs.
+// The next 32-wide k tile is loaded into registers while this one is used.
 template <int NB>
 __device__ void cross_item(const float *A, int64_t M, int64_t K, const float *B, int r,
                            int64_t m0, float *C, float *sm)
 {
-    constexpr int BM = kCrossRows, BK = 16, TM = BM / 16, TN = NB / 16;
-    float(*As)[BM + 4] = reinterpret_cast<float(*)[BM + 4]>(sm);
-    float(*Bs)[NB] = reinterpret_cast<float(*)[NB]>(sm + BK * (BM + 4));
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    float acc[TM][TN];
+    constexpr int BM = kCrossRows, BK = 32, TX = NB / 4, TY = kT / TX, TM = BM / TY;
+    constexpr int LDA = BK + 1;
+    constexpr int AL = BM * BK / kT, BL = (BK * NB + kT - 1) / kT;   // loads per thread
+    float *As = sm;                         // BM x LDA
+    float *Bs = sm + BM * LDA;              // BK x NB (16-byte aligned: BM * LDA % 4 == 0)
+    const int tid = threadIdx.x, ty = tid / TX, tx = tid - ty * TX;
+    float acc[TM][4];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j)
+        for (int j = 0; j < 4; ++j)
             acc[i][j] = 0.f;
+    float ra[AL], rb[BL];
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+        for (int q = 0; q < AL; ++q) {
+            const int idx = tid + kT * q, mm = idx / BK, kk = idx - mm * BK;
+            const int64_t gm = m0 + mm, gk = k0 + kk;
+            ra[q] = (gm < M && gk < K) ? A[gm * K + gk] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < BL; ++q) {
+            const int idx = tid + kT * q, kk = idx / NB, nn = idx - kk * NB;
+            const int64_t gk = k0 + kk;
+            rb[q] = (idx < BK * NB && nn < r && gk < K) ? B[gk * r + nn] : 0.f;
+        }
+    };
+    fetch(0);
     for (int64_t k0 = 0; k0 < K; k0 += BK) {
-        __syncthreads();
+        __syncthreads();   // the previous tile (or item) is no longer read
 #pragma unroll
-        for (int t = 0; t < BM * BK / kT; ++t) {
-            int idx = tid + t * kT;
-            int mm = idx >> 4, kk = idx & 15;
-            int64_t gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < K) ? A[gm * K + gk] : 0.f;
+        for (int q = 0; q < AL; ++q) {
+            const int idx = tid + kT * q, mm = idx / BK, kk = idx - mm * BK;
+            As[mm * LDA + kk] = ra[q];
         }
-        for (int idx = tid; idx < BK * NB; idx += kT) {
-            int kk = idx / NB, nn = idx - kk * NB;
-            int64_t gk = k0 + kk;
-            Bs[kk][nn] = (nn < r && gk < K) ? B[gk * r + nn] : 0.f;
+#pragma unroll
+        for (int q = 0; q < BL; ++q) {
+            const int idx = tid + kT * q;
+            if (idx < BK * NB)
+                Bs[idx] = rb[q];
         }
         __syncthreads();
-#pragma unroll
+        if (k0 + BK < K)
+            fetch(k0 + BK);
+#pragma unroll 8
         for (int kk = 0; kk < BK; ++kk) {
-            float a[TM], b[TN];
+            const float4 b = *reinterpret_cast<const float4 *>(Bs + kk * NB + tx * 4);
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
-                a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-            for (int j = 0; j < TN; ++j)
-                b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int j = 0; j < TN; ++j)
-                    acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            for (int i = 0; i < TM; ++i) {
+                const float a = As[(ty * TM + i) * LDA + kk];
+                acc[i][0] = fmaf(a, b.x, acc[i][0]);
+                acc[i][1] = fmaf(a, b.y, acc[i][1]);
+                acc[i][2] = fmaf(a, b.z, acc[i][2]);
+                acc[i][3] = fmaf(a, b.w, acc[i][3]);
+            }
         }
     }
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-        int64_t gm = m0 + ty + 16 * i;
+        const int64_t gm = m0 + ty * TM + i;
         if (gm >= M)
             continue;
 #pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            int n = tx + 16 * j;
+        for (int j = 0; j < 4; ++j) {
+            const int n = tx * 4 + j;
             if (n < r)
                 C[gm * r + n] = acc[i][j];
         }
     }
 }
 
-// Alg. 3 for rows [row0, row0 + kNnlsRows) of X; warp per row, Qt in shared
-// memory (the same iteration as the single-instance kernel)
-template <int J>
-__device__ void nnls_item(const float *Qt, const float *dv, const float *Cm, int64_t rows, int r,
-                          float alpha, float *X, int64_t row0, int nrows, const BatchNnls &o,
-                          float *sm, unsigned long long *iter_total, unsigned *status)
+// lanes per row of the grouped NQP solver for rank r <= 64 (J = 8 coordinates
+// per lane), and the rows of one NQP work item: `mult` rows per group of
+// every warp
+__host__ __device__ inline int nnls_lanes(int r) { return r <= 8 ? 1 : r <= 16 ? 2 : r <= 32 ? 4 : 8; }
+__host__ __device__ inline int64_t nnls_item_rows(int r, int mult)
 {
-    constexpr int RP = 32 * J;
-    float *Qs = sm;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *vb = sm + RP * RP + warp * RP;
-    const int r4 = (r + 3) & ~3;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < RP * RP; idx += kT) {
-        int i = idx / RP, j = idx - i * RP;
-        Qs[idx] = (i < r && j < r) ? Qt[i * r + j] : 0.f;
-    }
-    __syncthreads();
-    float iq[J], hq[J], dd[J];
-    bool live[J];
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-        int e = lane * J + j;
-        float qii = e < r ? Qs[e * RP + e] : 0.f;
-        live[j] = qii > 0.f;
-        iq[j] = live[j] ? 1.f / qii : 0.f;
-        hq[j] = 0.5f * qii;
-        dd[j] = (e < r && live[j]) ? dv[e] : 1.f;
-    }
-    const int T = o.cd_steps < 0 ? r : o.cd_steps;
-    auto matvec = [&](const float(&v)[J], float(&out)[J]) {
-#pragma unroll
-        for (int j = 0; j < J; ++j)
-            vb[lane * J + j] = v[j];
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < J; ++j)
-            out[j] = 0.f;
-        for (int k = 0; k < r4; ++k) {
-            const float vk = vb[k];
-#pragma unroll
-            for (int j = 0; j < J; ++j)
-                out[j] = fmaf(Qs[k * RP + lane * J + j], vk, out[j]);
-        }
-        __syncwarp();
-    };
-    auto proj_sq = [&](const float(&y)[J], const float(&g)[J]) {
-        float s = 0.f;
-#pragma unroll
-        for (int j = 0; j < J; ++j)
-            if (y[j] > 0.f || g[j] < 0.f)
-                s = fmaf(g[j], g[j], s);
-        return warp_sum(s);
-    };
-    unsigned long long my_iters = 0;
-    const int64_t rend = row0 + nrows < rows ? row0 + nrows : rows;
-    for (int64_t row = row0 + warp; row < rend; row += kWarps) {
-        float y[J], g[J];
-        bool ok = true;
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            int e = lane * J + j;
-            float c = 0.f, x0 = 0.f;
-            if (e < r) {
-                c = Cm[row * r + e];
-                x0 = X[row * r + e];
-                ok = ok && isfinite(c) && isfinite(x0);
-            }
-            g[j] = live[j] ? (alpha - c) / dd[j] : 0.f;
-            y[j] = live[j] ? x0 * dd[j] : 0.f;
-        }
-        if (!__all_sync(0xffffffffu, ok)) {
-            if (lane == 0)
-                atomicOr(status, kStNonFinite);
-            continue;
-        }
-        {
-            float t[J];
-            matvec(y, t);
-#pragma unroll
-            for (int j = 0; j < J; ++j)
-                g[j] = live[j] ? g[j] + t[j] : 0.f;
-        }
-        const float s0 = proj_sq(y, g);
-        int k = 0;
-        if (s0 > 0.f) {
-            for (k = 1; k <= o.max_inner; ++k) {
-                float gb[J], s = 0.f;
-#pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    gb[j] = (y[j] > 0.f || g[j] < 0.f) ? g[j] : 0.f;
-                    s = fmaf(gb[j], gb[j], s);
-                }
-                s = warp_sum(s);
-                if (s > 0.f) {
-                    float u[J];
-                    matvec(gb, u);
-                    float den = 0.f;
-#pragma unroll
-                    for (int j = 0; j < J; ++j)
-                        den = fmaf(gb[j], u[j], den);
-                    den = warp_sum(den);
-                    if (den > 0.f) {
-                        const float al = s / den;
-                        float dl[J];
-#pragma unroll
-                        for (int j = 0; j < J; ++j) {
-                            float yn = fmaxf(0.f, y[j] - al * gb[j]);
-                            dl[j] = yn - y[j];
-                            y[j] = yn;
-                        }
-                        matvec(dl, u);
-#pragma unroll
-                        for (int j = 0; j < J; ++j)
-                            g[j] += u[j];
-                    }
-                }
-                for (int t = 0; t < T; ++t) {
-                    unsigned bkey = 0u;
-                    int bj = 0;
-                    float bdel = 0.f;
-#pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        float del = fmaxf(0.f, fmaf(-g[j], iq[j], y[j])) - y[j];
-                        float gain = -(del * fmaf(hq[j], del, g[j]));
-                        unsigned key = __float_as_uint(fmaxf(gain, 0.f)) & 0x7fffffffu;
-                        if (key > bkey) {
-                            bkey = key;
-                            bj = j;
-                            bdel = del;
-                        }
-                    }
-                    const unsigned mx = __reduce_max_sync(0xffffffffu, bkey);
-                    if (mx == 0u)
-                        break;
-                    const int src = __ffs(__ballot_sync(0xffffffffu, bkey == mx)) - 1;
-                    const int pj = __shfl_sync(0xffffffffu, bj, src);
-                    const float dp = __shfl_sync(0xffffffffu, bdel, src);
-                    const int p = src * J + pj;
-#pragma unroll
-                    for (int j = 0; j < J; ++j)
-                        g[j] = fmaf(Qs[p * RP + lane * J + j], dp, g[j]);
-                    if (lane == src) {
-#pragma unroll
-                        for (int j = 0; j < J; ++j)
-                            if (j == pj)
-                                y[j] += dp;
-                    }
-                }
-                const float sk = proj_sq(y, g);
-                if (sk <= o.eps * s0)
-                    break;
-            }
-            if (k > o.max_inner)
-                k = o.max_inner;
-        }
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            int e = lane * J + j;
-            if (e < r)
-                X[row * r + e] = live[j] ? y[j] / dd[j] : 0.f;
-        }
-        if (lane == 0)
-            my_iters += (unsigned long long)k;
-    }
-    if (lane == 0 && my_iters)
-        atomicAdd(iter_total, my_iters);
+    return (int64_t)mult * kWarps * (32 / nnls_lanes(r));
+}
+
+// Alg. 3 for the rows of one work item (the grouped solver of k_nnls.cuh)
+template <int G>
+__device__ void nnls_item(const BatchInst &b, bool w_update, int64_t row0, int64_t nrows,
+                          const BatchArgs &a, float *sm)
+{
+    constexpr int RP = nnls_detail::Map<G, 8>::RP;
+    float *Qs = sm, *sd = sm + RP * RP;
+    const int r = b.r;
+    __syncthreads();   // the previous item's warps are done with the shared Qt
+    if (!nnls_detail::stage_qt<G, 8>(b.Qt, b.d, r, Qs, sd, a.status))
+        return;
+    NnlsArgs na{};
+    na.Qt = b.Qt;
+    na.d = b.d;
+    na.C = w_update ? b.Cw : b.Ch;
+    na.nsplit = 1;
+    na.rows = w_update ? b.m : b.n;
+    na.c_stride = na.rows * r;
+    na.r = r;
+    na.alpha = w_update ? b.alpha_w : b.alpha_h;
+    na.X = w_update ? b.W : b.Ht;
+    na.max_inner = a.nnls.max_inner;
+    na.eps = a.nnls.eps;
+    na.cd_steps = a.nnls.cd_steps;
+    na.iter_total = a.iter_total;
+    na.status = a.status;
+    const int64_t end = row0 + nrows < na.rows ? row0 + nrows : na.rows;
+    nnls_detail::nnls_rows<G, 8>(na, Qs, sd, sd + RP, row0 + (threadIdx.x >> 5), kWarps, end);
 }
 
 // ---- one phase over its items ---------------------------------------------
@@ -436,30 +327,31 @@ __device__ void run_phase(const BatchArgs &a, int phase, int64_t item_begin, int
             const int64_t M = w_update ? b.m : b.n, K = w_update ? b.n : b.m;
             const float *Bm = w_update ? b.Ht : b.W;
             float *C = w_update ? b.Cw : b.Ch;
-            if (r <= 32)
+            if (r <= 8)
+                cross_item<8>(A, M, K, Bm, r, local * kCrossRows, C, sm);
+            else if (r <= 16)
+                cross_item<16>(A, M, K, Bm, r, local * kCrossRows, C, sm);
+            else if (r <= 32)
                 cross_item<32>(A, M, K, Bm, r, local * kCrossRows, C, sm);
             else
                 cross_item<64>(A, M, K, Bm, r, local * kCrossRows, C, sm);
             break;
         }
         default: {
-            const int64_t rows = w_update ? b.m : b.n;
-            const float *C = w_update ? b.Cw : b.Ch;
-            float *X = w_update ? b.W : b.Ht;
-            const float al = w_update ? b.alpha_w : b.alpha_h;
-            if (r <= 32)
-                nnls_item<1>(b.Qt, b.d, C, rows, r, al, X, local * a.nnls_rows, a.nnls_rows,
-                             a.nnls, sm, a.iter_total, a.status);
-            else
-                nnls_item<2>(b.Qt, b.d, C, rows, r, al, X, local * a.nnls_rows, a.nnls_rows,
-                             a.nnls, sm, a.iter_total, a.status);
+            const int64_t nr = nnls_item_rows(r, a.nnls_rows);
+            switch (nnls_lanes(r)) {
+            case 1: nnls_item<1>(b, w_update, local * nr, nr, a, sm); break;
+            case 2: nnls_item<2>(b, w_update, local * nr, nr, a, sm); break;
+            case 4: nnls_item<4>(b, w_update, local * nr, nr, a, sm); break;
+            default: nnls_item<8>(b, w_update, local * nr, nr, a, sm); break;
+            }
             break;
         }
         }
     }
 }
 
-__global__ void __launch_bounds__(kT) k_batched_iter(const BatchArgs a)
+__global__ void __launch_bounds__(kT, 2) k_batched_iter(const BatchArgs a)
 {
     extern __shared__ __align__(16) float smem[];
     if (*(const volatile unsigned *)a.status & kStTimeout)
@@ -480,26 +372,30 @@ __global__ void __launch_bounds__(kT) k_batched_iter(const BatchArgs a)
 
 size_t batched_smem_bytes()
 {
-    // max over phases: NNLS Qt (64 x 64) + staging, Gram tile, cross tiles, rescale
-    const size_t nn = sizeof(float) * (64 * 64 + kWarps * 64);
-    const size_t gr = sizeof(float) * 32 * 64;
-    const size_t cr = sizeof(float) * (16 * (kCrossRows + 4) + 16 * 64);
-    const size_t rs = sizeof(float) * (64 * 64 + 64);
-    size_t m = nn;
-    m = gr > m ? gr : m;
-    m = cr > m ? cr : m;
-    m = rs > m ? rs : m;
+    // max over phases: grouped NQP solver (Qt, d, per-group buffers), Gram
+    // tile, cross tiles, rescale
+    auto nq = [](int rp, size_t pool) { return sizeof(float) * ((size_t)rp * rp + rp + pool); };
+    size_t m = nq(8, nnls_detail::pool_floats<1, 8>());
+    m = std::max(m, nq(16, nnls_detail::pool_floats<2, 8>()));
+    m = std::max(m, nq(32, nnls_detail::pool_floats<4, 8>()));
+    m = std::max(m, nq(64, nnls_detail::pool_floats<8, 8>()));
+    m = std::max(m, sizeof(float) * 32 * 64);
+    m = std::max(m, sizeof(float) * (kCrossRows * 33 + 32 * 64));
+    m = std::max(m, sizeof(float) * (64 * 64 + 64));
     return m;
 }
 
-int64_t batched_items(int phase, int64_t m, int64_t n, int nnls_rows)
+int64_t batched_items(int phase, int64_t m, int64_t n, int r, int nnls_mult)
 {
     const bool w = phase < 4;
     switch (phase & 3) {
     case 0: return ((w ? n : m) + kGramRows - 1) / kGramRows;
     case 1: return 1;
     case 2: return ((w ? m : n) + kCrossRows - 1) / kCrossRows;
-    default: return ((w ? m : n) + nnls_rows - 1) / nnls_rows;
+    default: {
+        const int64_t nr = nnls_item_rows(r, nnls_mult);
+        return ((w ? m : n) + nr - 1) / nr;
+    }
     }
 }
 
@@ -524,7 +420,9 @@ int batched_grid(bool cooperative)
 
 cudaError_t launch_batched(const BatchArgs &a, int grid, bool cooperative, cudaStream_t s)
 {
-    ProfScope prof_(KC_OTHER, s);
+    // a launch of a single phase is attributed to that phase's kernel class
+    static const KClass kPhaseClass[4] = {KC_GRAM, KC_RESCALE, KC_CROSS, KC_NNLS};
+    ProfScope prof_(a.phase_end == a.phase_begin + 1 ? kPhaseClass[a.phase_begin & 3] : KC_OTHER, s);
     const size_t smem = batched_smem_bytes();
     if (grid < 1)
         return cudaSuccess;

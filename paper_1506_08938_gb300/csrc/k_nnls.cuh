@@ -188,46 +188,62 @@ template <int G, int J>
 constexpr size_t smem_bytes()
 {
     using M = Map<G, J>;
-    return sizeof(float) *
-           ((size_t)M::RP * M::RP + M::RP + 2 * (size_t)kWarps * (32 / G) * M::VB);
+    return sizeof(float) * ((size_t)M::RP * M::RP + M::RP + 2 * (size_t)kWarps * (32 / G) * M::VB);
 }
 
 // CTAs per SM the register budget is sized for
 template <int J>
 constexpr int min_ctas() { return J >= 4 ? 3 : 4; }
 
+// Stage Qt (zero-padded to RP x RP) and the scale d (1 for dead and padding
+// coordinates) in shared memory; false (and the status flag) if Qt's
+// diagonal holds anything but 0 or 1.  All threads of the CTA take part.
 template <int G, int J>
-__global__ void __launch_bounds__(kWarps * 32, min_ctas<J>()) k_nnls(const NnlsArgs a)
+__device__ __forceinline__ bool stage_qt(const float *Qt, const float *d, int r, float *Qs,
+                                         float *sd, unsigned *status)
 {
-    using M = Map<G, J>;
-    constexpr int RP = M::RP;
-    constexpr int NG = 32 / G;            // rows per warp
-    extern __shared__ __align__(16) float smem[];
-    float *Qs = smem;                     // RP x RP
-    float *sd = Qs + RP * RP;             // scale d (1 for dead and padding)
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gi = lane / G, li = lane - gi * G;
-    float *vbg = sd + RP + (warp * NG + gi) * M::VB;                        // staging
-    float *ysg = sd + RP + (kWarps * NG + warp * NG + gi) * M::VB;          // iterate y
-    const int r = a.r;
-    const int r4 = (r + 3) & ~3;
-
+    constexpr int RP = Map<G, J>::RP;
     for (int idx = threadIdx.x; idx < RP * RP; idx += blockDim.x) {
         int i = idx / RP, j = idx - i * RP;
-        Qs[idx] = (i < r && j < r) ? a.Qt[i * r + j] : 0.f;
+        Qs[idx] = (i < r && j < r) ? Qt[i * r + j] : 0.f;
     }
     __syncthreads();
     bool bad = false;
     for (int e = threadIdx.x; e < RP; e += blockDim.x) {
         const float qii = Qs[e * RP + e];
         bad = bad || (qii != 0.f && qii != 1.f);
-        sd[e] = (e < r && qii > 0.f) ? a.d[e] : 1.f;
+        sd[e] = (e < r && qii > 0.f) ? d[e] : 1.f;
     }
     if (__syncthreads_or(bad)) {
-        if (threadIdx.x == 0 && a.status)
-            atomicOr(a.status, kStBadInput);
-        return;
+        if (threadIdx.x == 0 && status)
+            atomicOr(status, kStBadInput);
+        return false;
     }
+    return true;
+}
+
+// shared floats behind Qs and sd: per group, a staging buffer and the iterate
+template <int G, int J>
+constexpr int pool_floats() { return 2 * kWarps * (32 / G) * Map<G, J>::VB; }
+
+// Alg. 3 for rows first, first + stride, ... < end, taken in rounds by the
+// groups of this warp (the layout and schedule of the file header).  Qs, sd
+// staged by stage_qt; pool holds pool_floats<G, J>() floats.  Called by
+// every lane of the warp.
+template <int G, int J>
+__device__ __forceinline__ void nnls_rows(const NnlsArgs &a, const float *__restrict__ Qs,
+                                          const float *__restrict__ sd, float *pool,
+                                          int64_t first, int64_t stride, int64_t end)
+{
+    using M = Map<G, J>;
+    constexpr int RP = M::RP;
+    constexpr int NG = 32 / G;            // rows per warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gi = lane / G, li = lane - gi * G;
+    float *vbg = pool + (warp * NG + gi) * M::VB;                        // staging
+    float *ysg = pool + (kWarps * NG + warp * NG + gi) * M::VB;          // iterate y
+    const int r = a.r;
+    const int r4 = (r + 3) & ~3;
 
     // live coordinates (bit j: this lane's j-th); a dead one keeps y = g = 0
     unsigned live = 0;
@@ -238,8 +254,8 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<J>()) k_nnls(const NnlsA
             live |= 1u << j;
     }
     const int T = a.cd_steps < 0 ? r : a.cd_steps;
-    const int64_t nw = (int64_t)gridDim.x * kWarps;
-    int64_t next = (int64_t)blockIdx.x * kWarps + warp;   // this warp's rows: next, next + nw, ...
+    const int64_t nw = stride;
+    int64_t next = first;   // this warp's rows: next, next + nw, ...
     const unsigned below = (1u << (gi * G)) - 1u;          // ballot bits of the groups before gi
 
     float g[J], zero[J];
@@ -282,7 +298,7 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<J>()) k_nnls(const NnlsA
         bool fresh = false;
         if (need) {
             const int64_t cand = next + (int64_t)__popc(needb & below) * nw;
-            row = cand < a.rows ? cand : -1;
+            row = cand < end ? cand : -1;
             fresh = row >= 0;
             need = false;   // busy now, or the share is exhausted: idle for good
         }
@@ -443,6 +459,20 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<J>()) k_nnls(const NnlsA
         if (a.s_final_max && my_smax)
             atomicMax(a.s_final_max, my_smax);
     }
+}
+
+template <int G, int J>
+__global__ void __launch_bounds__(kWarps * 32, min_ctas<J>()) k_nnls(const NnlsArgs a)
+{
+    constexpr int RP = Map<G, J>::RP;
+    extern __shared__ __align__(16) float smem[];
+    float *Qs = smem;                     // RP x RP
+    float *sd = Qs + RP * RP;             // scale d
+    if (!stage_qt<G, J>(a.Qt, a.d, a.r, Qs, sd, a.status))
+        return;
+    const int warp = threadIdx.x >> 5;
+    nnls_rows<G, J>(a, Qs, sd, sd + RP, (int64_t)blockIdx.x * kWarps + warp,
+                    (int64_t)gridDim.x * kWarps, a.rows);
 }
 
 template <int G, int J>

@@ -151,7 +151,7 @@ struct BatchArgs {
     unsigned *bar_count, *bar_gen;
 };
 size_t batched_smem_bytes();
-int64_t batched_items(int phase, int64_t m, int64_t n, int nnls_rows);
+int64_t batched_items(int phase, int64_t m, int64_t n, int r, int nnls_mult);
 int batched_grid(bool cooperative);
 cudaError_t launch_batched(const BatchArgs &a, int grid, bool cooperative, cudaStream_t s);
 

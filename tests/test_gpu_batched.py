@@ -72,7 +72,8 @@ def test_launch_shapes_are_bitwise_equal(h):
     insts = make_instances(SHAPES * 2, seed=11)
     T, K = 8, 3
     ref, _ = run_batched(h, insts, T, K, "persistent", use_graph=False)
-    for mode, graph in (("persistent", True), ("loop", False), ("autotune", True)):
+    for mode, graph in (("persistent", True), ("loop", False), ("autotune", True),
+                        ("phases", False)):
         got, reps = run_batched(h, insts, T, K, mode, use_graph=graph)
         for (W, Ht), (Wr, Hr) in zip(got, ref):
             assert np.array_equal(W, Wr), mode
