@@ -404,10 +404,12 @@ def main():
     Ht = H0.clone()
     h = P.Handle(local_rank)
 
-    def opts(iters, eps, hist=None, target=0.0, fstar=0.0, check=CHECK_EVERY, prec="fp32"):
+    def opts(iters, eps, hist=None, target=0.0, fstar=0.0, check=CHECK_EVERY, prec="fp32",
+             maxstop=0):
         hp = hist.ctypes.data_as(C.POINTER(C.c_double)) if hist is not None else None
         return P.solve_opts(iters, rel_gap_target=target, f_star=fstar, beta_w=inst.beta_w,
-                            beta_h=inst.beta_h, nnls=P.nnls_opts(max_inner=50, eps=eps),
+                            beta_h=inst.beta_h,
+                            nnls=P.nnls_opts(max_inner=50, eps=eps, maxstop_mode=maxstop),
                             objective="direct", obj_hist=hp, check_every=check, prec=prec)
 
     if args.profile:
@@ -478,8 +480,10 @@ def main():
     # BF16 cross terms (one warm-up and one timed solve each; same J*)
     variants = {}
     if not args.no_variants:
-        for vp in ("tf32", "bf16"):
-            vo = opts(8 * T_CONF, 1e-3, target=GAP, fstar=jstar, prec=vp)
+        for vp in ("tf32", "bf16", "fp32_fastbreak"):
+            # fp32_fastbreak: FP32 with Alg. 3's maxStop fast break (previous-update reading)
+            vo = opts(8 * T_CONF, 1e-3, target=GAP, fstar=jstar, prec=vp.split("_")[0],
+                      maxstop=1 if vp.endswith("fastbreak") else 0)
 
             def vstep():
                 W.copy_(W0)
@@ -495,7 +499,8 @@ def main():
             v1.record()
             torch.cuda.synchronize()
             variants[vp] = {"ms_to_gap": v0.elapsed_time(v1), "iters": vr.iters_done,
-                            "reached": vr.rel_gap <= GAP, "final_gap": vr.rel_gap}
+                            "reached": vr.rel_gap <= GAP, "final_gap": vr.rel_gap,
+                            "kbar": vr.kbar}
 
     # ---- end to end through the C ABI with host buffers (pinned)
     Vh = torch.tensor(inst.V).pin_memory()

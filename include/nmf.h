@@ -105,9 +105,11 @@ typedef struct {
     double eps;          /* accelerated condition ||f_k||^2 <= eps ||f_0||^2,
                             f = projected gradient in the rescaled space [1e-3] */
     int cd_steps;        /* greedy coordinate steps per iteration, -1 = r [-1] */
-    int maxstop_mode;    /* fast-break rule of Alg. 3: 0 off; 1 = threshold is
-                            the largest final ||f||^2 of the previous update of
-                            the same factor (deterministic reading) [0]       */
+    int maxstop_mode;    /* fast-break rule of Alg. 3: 0 off; 1 = a row stops
+                            once ||f||^2 <= threshold; in nmf_solve the
+                            threshold is the largest final ||f||^2 of the
+                            previous update of the same factor (0 before the
+                            first), a deterministic reading [0]              */
     float maxstop;       /* threshold for mode 1 in nmf_nnls_update [0]       */
     int lanes;           /* lanes of a warp per row problem: 1, 2, 4, ..., 32
                             with lanes * 8 >= r; 0 = chosen from r [0]        */

@@ -628,7 +628,8 @@ struct HalfStep {
     float *Cs;          // cross slices
     int nsplit;
     float *Q;           // Q = G_other + beta I (kept for KKT)
-    unsigned *smax;     // maxStop bits for this factor
+    unsigned *ms_thr;   // maxStop mode 1: threshold of this update (float bits)
+    unsigned *ms_out;   //   and the largest final ||f~||^2 of this update
     int tc_mode;        // -1: CUDA-core FP32 cross term
     const void *Atc;    // tensor-core operand (F32, or the BF16 copy)
     int64_t lda_tc;
@@ -712,9 +713,16 @@ nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s)
     a.lanes = L.nn.lanes;
     a.iter_total = h->ctr;
     a.status = h->status;
-    if (L.nn.maxstop_mode == 1)
-        return NMF_E_NOTIMPL;   // threshold needs a device-side read; not wired yet
+    if (L.nn.maxstop_mode == 1) {
+        // fast break (Alg. 3, reading R11): stop a row once its ||f~||^2 is at
+        // most the largest final value of the previous update of this factor
+        CK(cudaMemsetAsync(s.ms_out, 0, sizeof(unsigned), st));
+        a.maxstop_dev = s.ms_thr;
+        a.s_final_max = s.ms_out;
+    }
     CK(launch_nnls(a, st));
+    if (L.nn.maxstop_mode == 1)
+        CK(cudaMemcpyAsync(s.ms_thr, s.ms_out, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
     return NMF_OK;
 }
 
@@ -916,8 +924,8 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     Loop L{};
     L.r = r;
     L.nn = opts_or_default(&o.nnls);
-    if (L.nn.maxstop_mode != 0)
-        return NMF_E_NOTIMPL;
+    if (L.nn.maxstop_mode < 0 || L.nn.maxstop_mode > 1)
+        return NMF_E_NOTIMPL;   // mode 2 (sequential, order-dependent) is the oracle's only
     {
         int lg = 0, lj = 0;
         if (!nnls_layout(r, L.nn.lanes, &lg, &lj))
@@ -1102,6 +1110,10 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
         hh.K = m;
         hh.nsplit = sh;
     }
+    hw.ms_thr = h->smax + 0;
+    hh.ms_thr = h->smax + 1;
+    hw.ms_out = h->smax + 2;
+    hh.ms_out = h->smax + 3;
     hw.tc_mode = hh.tc_mode = sparse ? -1 : mode;
     hw.pack = hh.pack = pack;
     if (mode >= 0) {
@@ -1123,6 +1135,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     CK(cudaMemsetAsync(h->ctr, 0, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(h->idev, 0, 2 * sizeof(int), s));
     CK(cudaMemsetAsync(L.ticket, 0, 4 * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(h->smax, 0, 4 * sizeof(unsigned), s));   // maxStop: 0 before the first update
     CK(cudaMemcpyAsync(&L.vv, vv_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
 

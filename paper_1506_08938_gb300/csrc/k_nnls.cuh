@@ -254,6 +254,9 @@ __device__ __forceinline__ void nnls_rows(const NnlsArgs &a, const float *__rest
             live |= 1u << j;
     }
     const int T = a.cd_steps < 0 ? r : a.cd_steps;
+    // fast-break threshold (mode 1): from device memory when the previous
+    // update of the same factor left it there
+    const float mstop = a.maxstop_dev ? __uint_as_float(*a.maxstop_dev) : a.maxstop;
     const int64_t nw = stride;
     int64_t next = first;   // this warp's rows: next, next + nw, ...
     const unsigned below = (1u << (gi * G)) - 1u;          // ballot bits of the groups before gi
@@ -444,7 +447,7 @@ __device__ __forceinline__ void nnls_rows(const NnlsArgs &a, const float *__rest
         const float sk = group_sum<G>(proj_part<J>(y, g));
         if (active) {
             ++k;
-            const bool stop = sk <= a.eps * s0 || (a.maxstop_mode == 1 && sk <= a.maxstop) ||
+            const bool stop = sk <= a.eps * s0 || (a.maxstop_mode == 1 && sk <= mstop) ||
                               k >= a.max_inner;
             if (stop) {
                 finish(sk);

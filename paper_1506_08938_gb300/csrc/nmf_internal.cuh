@@ -49,6 +49,7 @@ struct NnlsArgs {
     int cd_steps;           // < 0: r
     int maxstop_mode;
     float maxstop;          // threshold for mode 1
+    const unsigned *maxstop_dev;   // mode 1: threshold (float bits) in device memory, else null
     int32_t *iters;         // optional per-row counts
     unsigned long long *iter_total;   // optional sum of counts
     unsigned *s_final_max;  // optional: atomicMax of final ||f||^2 bits

@@ -523,3 +523,35 @@ def test_sharded_schedule_single_rank_on_gpu(h):
     tw, th = step_bounds(Wo, inst.Ht0, 10)
     assert rel_err(to_np(W), Wo) < tw
     assert rel_err(to_np(Ht), Ho) < th
+
+
+def test_solve_fast_break_previous_update(h):
+    """maxStop mode 1 inside the solve (Alg. 3's fast break, deterministic
+    reading: the threshold of an update is the largest final ||f~||^2 of the
+    previous update of the same factor, 0 before the first).  Against the
+    oracle's mode 1 on the damped instance: a row near a threshold may stop
+    one inner iteration apart in FP32 and FP64, moving J by a fraction of
+    that iteration's decrease, so each iteration's J agrees to 5% of the
+    oracle's decrease (plus the FP32 objective tolerance 1e-5); the fast
+    break must cut the inner iterations, to within 5% of the oracle's count."""
+    import ctypes as C
+    inst = f32_inst(WL.tiny(seed=0, r=10))
+    T, beta = 20, 10.0
+    out = {}
+    for mode in (0, 1):
+        W, Ht = t32(inst.W0), t32(inst.Ht0)
+        hist = np.zeros(T)
+        o = P.solve_opts(T, beta_w=beta, beta_h=beta, objective="direct",
+                         nnls=P.nnls_opts(max_inner=50, eps=1e-3, maxstop_mode=mode),
+                         obj_hist=hist.ctypes.data_as(C.POINTER(C.c_double)))
+        rep = P.nmf_solve(h, t32(inst.V), W, Ht, o)
+        out[mode] = (hist.copy(), rep.inner_total)
+    Wo, Ho, ho, tot = O.nmf_solve(inst.W0, inst.Ht0, T, V=inst.V, beta_w=beta, beta_h=beta,
+                                  opts=O.nqp_opts(max_inner=50, eps=1e-3, maxstop_mode=1))
+    J0 = O.objective_dense(inst.V, inst.W0, inst.Ht0, 0.0, 0.0, beta, beta)
+    oj = ho[1::2]
+    dec = np.abs(np.diff(np.concatenate([[J0], oj])))
+    dev = np.abs(out[1][0] - oj)
+    assert np.all(dev <= 0.05 * dec + 1e-5 * oj), (dev, dec)
+    assert out[1][1] < out[0][1]
+    assert abs(out[1][1] - tot) <= 0.05 * tot
