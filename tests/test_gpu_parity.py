@@ -555,3 +555,42 @@ def test_solve_fast_break_previous_update(h):
     assert np.all(dev <= 0.05 * dec + 1e-5 * oj), (dev, dec)
     assert out[1][1] < out[0][1]
     assert abs(out[1][1] - tot) <= 0.05 * tot
+
+
+# L1 (a) and L2 (b) weights on either factor or both (§3.5; reading R2: b is
+# the paper's 2 mu_2, so its mu_2 = 1e-2 cases are b = 0.02)
+PENALTIES = [(0.01, 0.0, 0.0, 0.0), (0.0, 0.01, 0.0, 0.0), (0.01, 0.01, 0.0, 0.0),
+             (0.0, 0.0, 0.02, 0.0), (0.0, 0.0, 0.0, 0.02), (0.0, 0.0, 0.02, 0.02),
+             (0.01, 0.01, 0.02, 0.02), (1.0, 0.0, 0.0, 0.0), (0.0, 0.5, 0.0, 1.0)]
+
+
+@pytest.mark.parametrize("aw,ah,bw,bh", PENALTIES)
+def test_penalty_grid_one_iteration(h, aw, ah, bw, bh):
+    """One outer iteration with L1/L2 weights on W, Ht or both, from the same
+    FP32 start: W rows by the fixed-K rule (its inputs are exact), Ht within
+    its bound plus kappa(Q_H) times the W error actually made, J within the
+    first-order bound of those errors (data and penalty terms)."""
+    inst = f32_inst(WL.tiny(seed=7, r=10))
+    inst.alpha_w, inst.alpha_h, inst.beta_w, inst.beta_h = aw, ah, bw, bh
+    K = 3
+    W, Ht, hist, rep = run_solve(h, inst, 1, K, objective="direct")
+    Wo, Ho, ho, _ = O.nmf_solve(inst.W0, inst.Ht0, 1, V=inst.V, alpha_w=aw, alpha_h=ah,
+                                beta_w=bw, beta_h=bh, opts=O.nqp_opts(max_inner=K, eps=0.0))
+    Qw = O.gram(inst.Ht0, bw)
+    Cw = O.cross_dense(inst.V, inst.Ht0)
+    Wg, Hg = to_np(W), to_np(Ht)
+    assert np.all(Wg >= 0) and np.all(Hg >= 0)
+    assert_fixed_k_rows(Wg, Wo, Qw, Cw, aw, nnls_tol(Qw, 10))
+    ew = max(nnls_tol(Qw, 10), rel_err(Wg, Wo))
+    Qh = O.gram(Wo, bh)
+    eh = nnls_tol(Qh, 10) + kappa(Qh) * ew
+    assert rel_err(Hg, Ho) < eh
+    # first-order bound: the data term as in j_bound, plus the penalty terms'
+    # changes (|sum dW| <= sqrt(m r) ||dW||, d||W||^2/2 <= ||W|| ||dW||)
+    nw, nh = np.linalg.norm(Wo), np.linalg.norm(Ho)
+    pen = (aw * np.sqrt(Wo.size) * ew * nw + ah * np.sqrt(Ho.size) * eh * nh +
+           bw * nw * nw * ew + bh * nh * nh * eh)
+    jb = j_bound(inst, Wo, Ho, ew, eh) * O.objective_dense(inst.V, Wo, Ho) + pen
+    assert abs(hist[0] - ho[1]) < max(1e-5 * ho[1], jb)
+    if aw >= 1.0:   # a strong L1 weight zeroes entries of W on both sides
+        assert np.mean(Wg == 0) > 0.0 and np.mean(Wo == 0) > 0.0
