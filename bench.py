@@ -345,6 +345,60 @@ def sparse_measurement(P, torch, dev, h, seed):
             "note": "trace-identity gap tests (CSR V); BF16 values, FP32 accumulation"}
 
 
+def profile_part(part, P, WL, torch, dev, h, seed):
+    """One bounded piece of a measurement, for ncu launch lists and captures."""
+    import ctypes as C
+
+    import numpy as np
+    if part == "serve":
+        wl = WL.serving(seed=seed, rows=SERVE_ROWS, r=SERVE_R, rate=SERVE_RATE, duration=0.5,
+                        max_requests=64)
+        srv = P.Server(torch.tensor(wl.W, device=dev), slots=8, max_batch_cols=16384,
+                       max_batch_nnz=1 << 21, hbm_budget=2 << 30,
+                       nnls=P.nnls_opts(max_inner=50, eps=1e-3))
+        for rq in wl.requests[:4]:
+            srv.wait(srv.submit(*rq)[0])
+        torch.cuda.nvtx.range_push("profiled")
+        tickets = [srv.submit(*rq)[0] for rq in wl.requests]
+        for t in tickets:
+            srv.wait(t)
+        torch.cuda.nvtx.range_pop()
+        srv.close()
+    elif part == "batched":
+        insts = WL.batched(seed=seed, count=BATCH_COUNT, workers=max(1, os.cpu_count() or 1))
+        dv = []
+        for inst in insts:
+            V = torch.from_numpy(inst.V).to(dev)
+            dv.append((V, V.t().contiguous(), torch.from_numpy(inst.W0).to(dev),
+                       torch.from_numpy(inst.Ht0).to(dev)))
+        nn = P.nnls_opts(max_inner=50, eps=1e-3)
+        P.nmf_solve_batched(h, dv, P.solve_opts(3, nnls=nn, use_graph=False), mode="persistent")
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled")
+        P.nmf_solve_batched(h, dv, P.solve_opts(3, nnls=nn, use_graph=False), mode="persistent")
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    else:
+        sp = WL.sparse(seed=seed)
+        d = lambda a, dt: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        parts = (d(sp.rowptr, torch.int64), d(sp.colidx, torch.int32),
+                 d(sp.vals, torch.bfloat16), sp.n)
+        tparts = (d(sp.t_rowptr, torch.int64), d(sp.t_colidx, torch.int32),
+                  d(sp.t_vals, torch.bfloat16), sp.m)
+        W, Ht = d(sp.W0, torch.float32), d(sp.Ht0, torch.float32)
+        o = P.solve_opts(20, alpha_h=sp.alpha_h, nnls=P.nnls_opts(max_inner=50, eps=1e-3),
+                         check_every=0)
+        P.nmf_solve(h, None, W, Ht, o, csr_parts=parts, csr_t_parts=tparts)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled")
+        o = P.solve_opts(5, alpha_h=sp.alpha_h, nnls=P.nnls_opts(max_inner=50, eps=1e-3),
+                         check_every=0)
+        P.nmf_solve(h, None, W, Ht, o, csr_parts=parts, csr_t_parts=tparts)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_part": part, "ok": True}))
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -364,6 +418,10 @@ def main():
     ap.add_argument("--no-sparse", action="store_true", help="skip the sparse measurement")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the TF32 / BF16 time-to-gap variants")
+    ap.add_argument("--profile-part", choices=["serve", "batched", "sparse"],
+                    help="for ncu: a short run of one measurement (0.5 s of serving, 3 "
+                         "batched iterations, 5 sparse iterations) inside NVTX range "
+                         "'profiled', then exit")
     ap.add_argument("--profile", action="store_true",
                     help="for ncu: 300 warm outer iterations, then 10 inside NVTX range "
                          "'profiled'; prints per-kernel-class times and exits")
@@ -394,6 +452,9 @@ def main():
             dist.barrier()
 
     dev = torch.device("cuda", local_rank)
+    if args.profile_part:
+        profile_part(args.profile_part, P, WL, torch, dev, P.Handle(local_rank), args.seed)
+        return
     inst = WL.dense(seed=args.seed)
     m, n, r = inst.m, inst.n, inst.r
     V = torch.tensor(inst.V, device=dev)
