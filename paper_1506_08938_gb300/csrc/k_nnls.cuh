@@ -523,6 +523,8 @@ cudaError_t launch(const NnlsArgs &a, cudaStream_t s)
     const int grid = (int)(need < cap ? need : cap);
     if (grid < 1)
         return cudaSuccess;
+    // an ordinary launch: started early beside the tensor-core kernel's tail
+    // this latency-bound kernel measured slower, not faster
     k_nnls<G, J><<<grid, kWarps * 32, smem_bytes<G, J>(), s>>>(a);
     count_launch();
     return cudaGetLastError();

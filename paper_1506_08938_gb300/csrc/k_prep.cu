@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(kThreads) k_factor_prep(const PrepArgs a)
 {
     constexpr int T = NB / 16;
     __shared__ float Xs[kRowsBlock][NB + 1];
+    pdl_trigger();   // the finishing kernel may launch; it waits for these partials
     const int r = a.r, tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
     const int64_t k0 = (int64_t)blockIdx.x * a.chunk;
     const int64_t k1 = k0 + a.chunk < a.rows ? k0 + a.chunk : a.rows;
@@ -104,6 +105,8 @@ __global__ void __launch_bounds__(kSumWarps * 32) k_prep_finish(const PrepArgs a
     __shared__ float part[kSumWarps][33];
     __shared__ float sd[kMaxRank];
     __shared__ int last;
+    pdl_trigger();
+    pdl_wait();   // the partials are the previous kernel's output
     const int r = a.r, n = r * r;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int e = blockIdx.x * 32 + lane;
@@ -202,6 +205,8 @@ cudaError_t launch_factor_prep(const PrepArgs &a0, cudaStream_t s)
         return cudaErrorInvalidValue;
     a.chunk = prep_chunk(a.rows);
     const int S = prep_slices(a.rows);
+    // the partials kernel follows the latency-bound NQP kernel: an ordinary
+    // launch; the finishing kernel may start while the partials drain
     if (a.r <= 32)
         k_factor_prep<32><<<S, kThreads, 0, s>>>(a);
     else if (a.r <= 64)
@@ -209,10 +214,13 @@ cudaError_t launch_factor_prep(const PrepArgs &a0, cudaStream_t s)
     else
         k_factor_prep<128><<<S, kThreads, 0, s>>>(a);
     count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
     const int n = a.r * a.r;
-    k_prep_finish<<<(n + 31) / 32, kSumWarps * 32, 0, s>>>(a, S);
+    e = pdl_launch(k_prep_finish, dim3((n + 31) / 32), dim3(kSumWarps * 32), 0, s, a, S);
     count_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace nmfi

@@ -301,9 +301,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    pdl_trigger();
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
+            // A (the data matrix) is written by no earlier kernel: the first
+            // stages' A tiles are requested before waiting for the previous
+            // kernel, whose output the packed factor B is
+            const int64_t pre = it1 - it0 < STAGES ? it1 - it0 : STAGES;
+            {
+                int tile = tile0, kb = kb0 - 1;
+                for (int64_t i = 0; i < pre; ++i) {
+                    if (++kb == KB) {
+                        kb = 0;
+                        ++tile;
+                    }
+                    mbar_expect_tx(&full[i], TX_BYTES);
+                    tma_load_2d(A(i), &tmA, &full[i], kb * KSTEP_ELEMS, tile * 128);
+                }
+            }
+            pdl_wait();
             int stage = 0;
             uint32_t phase = 0;
             int tile = tile0, kb = kb0 - 1;
@@ -312,10 +329,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     kb = 0;
                     ++tile;
                 }
-                if (!mbar_wait(&empty[stage], phase ^ 1u, deadline, abort_flag))
-                    break;
-                mbar_expect_tx(&full[stage], TX_BYTES);
-                tma_load_2d(A(stage), &tmA, &full[stage], kb * KSTEP_ELEMS, tile * 128);
+                if (it - it0 >= pre) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, deadline, abort_flag))
+                        break;
+                    mbar_expect_tx(&full[stage], TX_BYTES);
+                    tma_load_2d(A(stage), &tmA, &full[stage], kb * KSTEP_ELEMS, tile * 128);
+                }
                 tma_load_2d(B(stage), &tmB, &full[stage], kb * KSTEP_ELEMS, 0);
                 if (++stage == STAGES) {
                     stage = 0;
@@ -697,9 +716,9 @@ cudaError_t launch_mode(const CUtensorMap &a, const CUtensorMap &b, const TcArgs
             return e;
         attr = true;
     }
-    kern<<<p.grid, kThreads, C::SMEM, s>>>(a, b, p);
+    cudaError_t e = pdl_launch(kern, dim3(p.grid), dim3(kThreads), C::SMEM, s, a, b, p);
     count_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 template <int MODE>

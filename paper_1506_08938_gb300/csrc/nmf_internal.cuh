@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/nmf.h"
 
 #define NMF_API extern "C" __attribute__((visibility("default")))
@@ -19,6 +21,34 @@ constexpr unsigned kStTimeout = 2u;
 constexpr unsigned kStBadInput = 4u;   // an argument in device memory broke its contract
 
 void count_launch(int n = 1);
+
+// Programmatic dependent launch: a kernel launched with pdl_launch may start
+// (prologue, loads of inputs no earlier kernel writes) while the previous
+// kernel on the stream drains; it must pass pdl_wait() before it reads that
+// kernel's outputs or writes anything an earlier kernel may still read.
+// Without the launch attribute both calls are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Per-kernel-class device time (CUDA events around launches while enabled).
 enum KClass { KC_GRAM = 0, KC_CROSS, KC_SPMM, KC_RESCALE, KC_NNLS, KC_OBJECTIVE, KC_OTHER,
