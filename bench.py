@@ -293,6 +293,73 @@ def batched_measurement(P, torch, dev, h, seed, iters=20, warmup=3):
 
 
 SPARSE_T = 100     # outer iterations of the sparse configuration
+TINY_T = 50        # outer iterations of the tiny configuration
+
+
+def tiny_measurement(P, torch, dev, h, seed):
+    """Tiny dense configuration (V = W0 H0 + |N(0,0.01)|, 200 x 150, r = 10):
+    time to (J - J*)/J* <= 1e-4 on the GPU and, as full runs on the host, for
+    the FP64 oracle; each side's J* is the minimum of its own 4 x 50-iteration
+    run at eps 1e-6."""
+    import ctypes as C
+
+    import numpy as np
+
+    import workloads as WL
+    inst = WL.tiny(seed=seed, r=10)
+    V = torch.tensor(inst.V, dtype=torch.float32, device=dev)
+    W0 = torch.tensor(inst.W0, dtype=torch.float32, device=dev)
+    H0 = torch.tensor(inst.Ht0, dtype=torch.float32, device=dev)
+    W, Ht = W0.clone(), H0.clone()
+
+    def solve(iters, eps, hist=None, target=0.0, fstar=0.0):
+        hp = hist.ctypes.data_as(C.POINTER(C.c_double)) if hist is not None else None
+        o = P.solve_opts(iters, rel_gap_target=target, f_star=fstar, objective="direct",
+                         nnls=P.nnls_opts(max_inner=50, eps=eps), obj_hist=hp,
+                         check_every=CHECK_EVERY)
+        W.copy_(W0)
+        Ht.copy_(H0)
+        return P.nmf_solve(h, V, W, Ht, o)
+
+    ref = np.zeros(4 * TINY_T)
+    solve(4 * TINY_T, 1e-6, hist=ref)
+    jstar = float(ref.min())
+    solve(8 * TINY_T, 1e-3, target=GAP, fstar=jstar)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rep = solve(8 * TINY_T, 1e-3, target=GAP, fstar=jstar)
+    e1.record()
+    torch.cuda.synchronize()
+    return {"workload": "tiny200x150r10", "ms_to_gap": e0.elapsed_time(e1),
+            "iters": rep.iters_done, "reached": rep.rel_gap <= GAP, "J_star": jstar,
+            "note": "launch-bound (one graph replay per iteration, adaptive gap tests); "
+                    "the FP64 oracle's full run is in cpu_baseline.tiny"}
+
+
+def oracle_tiny_to_gap(seed):
+    """The FP64 oracle on the tiny configuration, full runs on the host: its
+    own J* (minimum over 4 x 50 iterations at eps 1e-6), then a timed run to
+    the first iteration within the gap."""
+    import numpy as np
+
+    import oracle as O
+    import workloads as WL
+    inst = WL.tiny(seed=seed, r=10)
+    Vd = inst.V.astype(np.float64)
+    _, _, oref, _ = O.nmf_solve(inst.W0, inst.Ht0, 4 * TINY_T, V=Vd,
+                                opts=O.nqp_opts(max_inner=50, eps=1e-6))
+    jstar = float(oref[1::2].min())
+    _, _, oh, _ = O.nmf_solve(inst.W0, inst.Ht0, 8 * TINY_T, V=Vd,
+                              opts=O.nqp_opts(max_inner=50, eps=1e-3))
+    hit = np.nonzero((oh[1::2] - jstar) / jstar <= GAP)[0]
+    t_gap = int(hit[0]) + 1 if len(hit) else 8 * TINY_T
+    t0 = time.perf_counter()
+    O.nmf_solve(inst.W0, inst.Ht0, t_gap, V=Vd, opts=O.nqp_opts(max_inner=50, eps=1e-3))
+    return {"workload": "tiny200x150r10", "ms_to_gap": (time.perf_counter() - t0) * 1e3,
+            "iters": t_gap, "J_star": jstar, "cores": O.num_threads(),
+            "sample": "full oracle run to its own gap"}
 
 
 def sparse_measurement(P, torch, dev, h, seed):
@@ -416,6 +483,7 @@ def main():
                     help="skip the many-instance measurement")
     ap.add_argument("--batched-iters", type=int, default=20)
     ap.add_argument("--no-sparse", action="store_true", help="skip the sparse measurement")
+    ap.add_argument("--no-tiny", action="store_true", help="skip the tiny-configuration measurement")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the TF32 / BF16 time-to-gap variants")
     ap.add_argument("--profile-part", choices=["serve", "batched", "sparse"],
@@ -590,6 +658,7 @@ def main():
     batched = None if args.no_batched else batched_measurement(P, torch, dev, h, args.seed,
                                                                iters=args.batched_iters)
     sparse = None if args.no_sparse else sparse_measurement(P, torch, dev, h, args.seed)
+    tiny = None if (args.no_tiny or rank != 0) else tiny_measurement(P, torch, dev, h, args.seed)
     fp32_peak = P.nmf_peak_fp32()   # measured: independent FFMA chains on every SM
     if rank != 0:
         return
@@ -651,7 +720,8 @@ def main():
                "the iteration count of this GPU run (oracle trajectory file missing)")
         cpu = {"value": s * tg * 1e3, "unit": "ms", "cores": cores, "kind": "oracle",
                "sample": f"1 outer iteration of the FP64 oracle on the full workload "
-                         f"({s:.2f} s) x {tg} iterations to the gap, {src}"}
+                         f"({s:.2f} s) x {tg} iterations to the gap, {src}",
+               "tiny": oracle_tiny_to_gap(args.seed)}
 
     out = {
         "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -669,6 +739,7 @@ def main():
         "serve": serve,
         "batched": batched,
         "sparse": sparse,
+        "tiny": tiny,
         "fp32_peak_tflops_measured": fp32_peak,
         "gpu_launches": launches,
         "roofline": roof,
