@@ -112,7 +112,7 @@ typedef struct {
                             first), a deterministic reading [0]              */
     float maxstop;       /* threshold for mode 1 in nmf_nnls_update [0]       */
     int lanes;           /* lanes of a warp per row problem: 1, 2, 4, ..., 32
-                            with lanes * 8 >= r; 0 = chosen from r [0]        */
+                            with lanes * 16 >= r; 0 = chosen from r [0]       */
 } nmf_nnls_opts;
 
 /* Options of the outer loop (Alg. 1 / Alg. 2). */

@@ -290,7 +290,9 @@ __device__ void nnls_item(const BatchInst &b, bool w_update, int64_t row0, int64
     na.iter_total = a.iter_total;
     na.status = a.status;
     const int64_t end = row0 + nrows < na.rows ? row0 + nrows : na.rows;
-    nnls_detail::nnls_rows<G, 8>(na, Qs, sd, sd + RP, row0 + (threadIdx.x >> 5), kWarps, end);
+    nnls_detail::flush_warp_counters(
+        na, nnls_detail::nnls_rows<G, 8>(na, Qs, sd, sd + RP, row0 + (threadIdx.x >> 5), kWarps,
+                                         end));
 }
 
 // ---- one phase over its items ---------------------------------------------

@@ -6,8 +6,8 @@ namespace nmfi {
 
 // G: explicit (1, 2, 4, ..., 32) or, for lanes == 0, the fewest lanes that
 // keep J <= 8 (fewest shuffles per coordinate step); J: the smallest of
-// 2, 4, 8 with G * J >= r and G * J >= 4.  Depends on r and lanes only, so a
-// row's result never depends on how many rows share the launch.
+// 2, 4, 8, 16 with G * J >= r and G * J >= 4.  Depends on r and lanes only,
+// so a row's result never depends on how many rows share the launch.
 bool nnls_layout(int r, int lanes, int *G, int *J)
 {
     int g = lanes;
@@ -19,7 +19,7 @@ bool nnls_layout(int r, int lanes, int *G, int *J)
     }
     if (g < 1 || g > 32 || (g & (g - 1)))
         return false;
-    for (int j = 2; j <= 8; j <<= 1)
+    for (int j = 2; j <= 16; j <<= 1)
         if (g * j >= r && g * j >= 4) {
             *G = g;
             *J = j;
@@ -36,7 +36,8 @@ static cudaError_t nnls_go(const NnlsArgs &a, int r, int lanes, bool prep_only, 
     switch (J) {
     case 2: return nnls_dispatch_j2(a, G, prep_only, s);
     case 4: return nnls_dispatch_j4(a, G, prep_only, s);
-    default: return nnls_dispatch_j8(a, G, prep_only, s);
+    case 8: return nnls_dispatch_j8(a, G, prep_only, s);
+    default: return nnls_dispatch_j16(a, G, prep_only, s);
     }
 }
 

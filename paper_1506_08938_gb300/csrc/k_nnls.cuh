@@ -141,6 +141,7 @@ __device__ __forceinline__ void matvec_buf(const float *__restrict__ Qs, const f
 #pragma unroll
     for (int j = 0; j < J; ++j)
         out[j] = 0.f;
+#pragma unroll 2
     for (int k = 0; k < r4; k += 4) {
         const float4 vk = *reinterpret_cast<const float4 *>(vg + k);
         float a0[J], a1[J];
@@ -193,7 +194,7 @@ constexpr size_t smem_bytes()
 
 // CTAs per SM the register budget is sized for
 template <int J>
-constexpr int min_ctas() { return J >= 4 ? 3 : 4; }
+constexpr int min_ctas() { return J >= 16 ? 2 : (J >= 4 ? 3 : 4); }
 
 // Stage Qt (zero-padded to RP x RP) and the scale d (1 for dead and padding
 // coordinates) in shared memory; false (and the status flag) if Qt's
@@ -203,9 +204,20 @@ __device__ __forceinline__ bool stage_qt(const float *Qt, const float *d, int r,
                                          float *sd, unsigned *status)
 {
     constexpr int RP = Map<G, J>::RP;
-    for (int idx = threadIdx.x; idx < RP * RP; idx += blockDim.x) {
-        int i = idx / RP, j = idx - i * RP;
-        Qs[idx] = (i < r && j < r) ? Qt[i * r + j] : 0.f;
+    constexpr int B = 8;   // loads in flight per thread before their stores
+    for (int base = threadIdx.x; base < RP * RP; base += B * blockDim.x) {
+        float v[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int idx = base + b * blockDim.x, i = idx / RP, j = idx % RP;
+            v[b] = (idx < RP * RP && i < r && j < r) ? Qt[i * r + j] : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int idx = base + b * blockDim.x;
+            if (idx < RP * RP)
+                Qs[idx] = v[b];
+        }
     }
     __syncthreads();
     bool bad = false;
@@ -226,14 +238,19 @@ __device__ __forceinline__ bool stage_qt(const float *Qt, const float *d, int r,
 template <int G, int J>
 constexpr int pool_floats() { return 2 * kWarps * (32 / G) * Map<G, J>::VB; }
 
-// Alg. 3 for rows first, first + stride, ... < end, taken in rounds by the
-// groups of this warp (the layout and schedule of the file header).  Qs, sd
-// staged by stage_qt; pool holds pool_floats<G, J>() floats.  Called by
-// every lane of the warp.
+// Alg. 3 for this warp's share of the rows, taken in rounds by its groups
+// (the layout and schedule of the file header).  The share is the runs of
+// `chunk` consecutive rows starting at first, first + stride, first +
+// 2 stride, ..., cut at end: its s-th row is first + (s / chunk) stride +
+// s % chunk (chunk a power of two, at most stride).  Qs, sd staged by
+// stage_qt; pool holds pool_floats<G, J>() floats.  Called by every lane of
+// the warp; returns the warp's (inner iterations, largest final ||P||^2
+// bits) for the counters of NnlsArgs, which the caller adds.
 template <int G, int J>
-__device__ __forceinline__ void nnls_rows(const NnlsArgs &a, const float *__restrict__ Qs,
+__device__ __forceinline__ uint2 nnls_rows(const NnlsArgs &a, const float *__restrict__ Qs,
                                           const float *__restrict__ sd, float *pool,
-                                          int64_t first, int64_t stride, int64_t end)
+                                          int64_t first, int64_t stride, int64_t end,
+                                          int chunk = 1)
 {
     using M = Map<G, J>;
     constexpr int RP = M::RP;
@@ -257,8 +274,8 @@ __device__ __forceinline__ void nnls_rows(const NnlsArgs &a, const float *__rest
     // fast-break threshold (mode 1): from device memory when the previous
     // update of the same factor left it there
     const float mstop = a.maxstop_dev ? __uint_as_float(*a.maxstop_dev) : a.maxstop;
-    const int64_t nw = stride;
-    int64_t next = first;   // this warp's rows: next, next + nw, ...
+    int64_t taken = 0;      // rows of the share handed out so far
+    const int csh = __ffs(chunk) - 1;
     const unsigned below = (1u << (gi * G)) - 1u;          // ballot bits of the groups before gi
 
     float g[J], zero[J];
@@ -300,12 +317,13 @@ __device__ __forceinline__ void nnls_rows(const NnlsArgs &a, const float *__rest
         const unsigned needb = __ballot_sync(kFull, need && li == 0);
         bool fresh = false;
         if (need) {
-            const int64_t cand = next + (int64_t)__popc(needb & below) * nw;
+            const int64_t sidx = taken + __popc(needb & below);
+            const int64_t cand = first + (sidx >> csh) * stride + (sidx & (chunk - 1));
             row = cand < end ? cand : -1;
             fresh = row >= 0;
             need = false;   // busy now, or the share is exhausted: idle for good
         }
-        next += (int64_t)__popc(needb) * nw;
+        taken += __popc(needb);
         if (!__any_sync(kFull, fresh || active))
             break;
 
@@ -313,21 +331,35 @@ __device__ __forceinline__ void nnls_rows(const NnlsArgs &a, const float *__rest
         if (__any_sync(kFull, fresh)) {
             bool ok = true;
             if (fresh) {
-                float y0[J];
+                // every load of a slice issued before the first add (the
+                // slices are summed in order, as one scalar chain would)
+                float c[J], x0[J], y0[J];
+                const float *xr = a.X + row * r, *cr = a.C + row * r;
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
                     const int e = M::coord(li, j);
-                    float c = 0.f, x0 = 0.f;
-                    if (e < r) {
-                        const float *cp = a.C + row * r + e;
-                        for (int s = 0; s < a.nsplit; ++s)
-                            c += cp[s * a.c_stride];
-                        x0 = a.X[row * r + e];
-                        ok = ok && isfinite(c) && isfinite(x0);
+                    x0[j] = e < r ? xr[e] : 0.f;
+                    c[j] = 0.f;
+                }
+                for (int s = 0; s < a.nsplit; ++s) {
+                    float t[J];
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const int e = M::coord(li, j);
+                        t[j] = e < r ? cr[(int64_t)s * a.c_stride + e] : 0.f;
                     }
+#pragma unroll
+                    for (int j = 0; j < J; ++j)
+                        c[j] += t[j];
+                }
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const int e = M::coord(li, j);
+                    if (e < r)
+                        ok = ok && isfinite(c[j]) && isfinite(x0[j]);
                     const bool lv = (live >> j) & 1u;
-                    g[j] = lv ? (a.alpha - c) / sd[e] : 0.f;   // q staged in g
-                    y0[j] = lv ? x0 * sd[e] : 0.f;
+                    g[j] = lv ? (a.alpha - c[j]) / sd[e] : 0.f;   // q staged in g
+                    y0[j] = lv ? x0[j] * sd[e] : 0.f;
                 }
                 st_lane<G, J>(ysg, li, y0);
             }
@@ -456,11 +488,25 @@ __device__ __forceinline__ void nnls_rows(const NnlsArgs &a, const float *__rest
             }
         }
     }
-    if (li == 0) {
-        if (a.iter_total && my_iters)
-            atomicAdd(a.iter_total, (unsigned long long)my_iters);
-        if (a.s_final_max && my_smax)
-            atomicMax(a.s_final_max, my_smax);
+    // the warp's total of inner iterations and largest final ||P||^2 (bits
+    // of a non-negative float: unsigned order is float order), in every lane
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_iters += __shfl_xor_sync(kFull, my_iters, o);
+        const unsigned t = __shfl_xor_sync(kFull, my_smax, o);
+        my_smax = t > my_smax ? t : my_smax;
+    }
+    return make_uint2(my_iters, my_smax);
+}
+
+// the counters of NnlsArgs from per-warp totals: one atomic per warp
+__device__ __forceinline__ void flush_warp_counters(const NnlsArgs &a, uint2 t)
+{
+    if ((threadIdx.x & 31) == 0) {
+        if (a.iter_total && t.x)
+            atomicAdd(a.iter_total, (unsigned long long)t.x);
+        if (a.s_final_max && t.y)
+            atomicMax(a.s_final_max, t.y);
     }
 }
 
@@ -473,9 +519,28 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<J>()) k_nnls(const NnlsA
     float *sd = Qs + RP * RP;             // scale d
     if (!stage_qt<G, J>(a.Qt, a.d, a.r, Qs, sd, a.status))
         return;
+    // this CTA's rows: a balanced contiguous range; warp w takes runs of
+    // 32 / G rows (one per group) at lo + w * 32 / G, every kWarps runs
+    constexpr int NG = 32 / G;
     const int warp = threadIdx.x >> 5;
-    nnls_rows<G, J>(a, Qs, sd, sd + RP, (int64_t)blockIdx.x * kWarps + warp,
-                    (int64_t)gridDim.x * kWarps, a.rows);
+    const int64_t lo = (int64_t)blockIdx.x * a.rows / gridDim.x;
+    const int64_t hi = (int64_t)(blockIdx.x + 1) * a.rows / gridDim.x;
+    const uint2 t = nnls_rows<G, J>(a, Qs, sd, sd + RP, lo + (int64_t)warp * NG,
+                                    (int64_t)kWarps * NG, hi, NG);
+    // one atomic per CTA on each counter (all rows of a launch would
+    // otherwise queue on the same two addresses)
+    __shared__ uint2 wt[kWarps];
+    if ((threadIdx.x & 31) == 0)
+        wt[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint2 c = wt[0];
+        for (int w = 1; w < kWarps; ++w) {
+            c.x += wt[w].x;
+            c.y = wt[w].y > c.y ? wt[w].y : c.y;
+        }
+        flush_warp_counters(a, c);
+    }
 }
 
 template <int G, int J>
@@ -511,16 +576,44 @@ cudaError_t prepare()
     return cudaSuccess;
 }
 
+// Grid of the standalone solver: sms * k CTAs (k <= the CTAs per SM that fit)
+// over balanced contiguous row ranges.  The groups of a warp run in lockstep,
+// so a warp costs its SM the same issue slots with one busy group as with
+// all of them: with w = ceil(rows per CTA / rows per warp) warp-rounds per
+// CTA, the busiest SM issues k w warp-rounds (what bounds an issue-bound
+// launch) and a warp runs ceil(w / kWarps) rounds in sequence (what bounds a
+// latency-bound one).  One round of the dependent chain of Alg. 3's steps
+// is taken as worth kLatRounds warp-rounds of issue; the smallest maximum of
+// the two wins, then the fewer warp-rounds, then the larger k.
+constexpr int64_t kLatRounds = 8;
+
+inline int nnls_grid(int64_t rows, int NG, int sms, int bps)
+{
+    int best_k = 1;
+    int64_t best_cost = -1, best_wr = 0;
+    for (int k = 1; k <= bps; ++k) {
+        const int64_t g = (int64_t)sms * k;
+        const int64_t rpc = (rows + g - 1) / g;
+        const int64_t w = (rpc + NG - 1) / NG;
+        const int64_t wr = k * w, rounds = (w + kWarps - 1) / kWarps;
+        const int64_t cost = wr > kLatRounds * rounds ? wr : kLatRounds * rounds;
+        if (best_cost < 0 || cost < best_cost || (cost == best_cost && wr <= best_wr)) {
+            best_k = k;
+            best_cost = cost;
+            best_wr = wr;
+        }
+    }
+    const int64_t g = (int64_t)sms * best_k;
+    return (int)(rows < g ? rows : g);
+}
+
 template <int G, int J>
 cudaError_t launch(const NnlsArgs &a, cudaStream_t s)
 {
     cudaError_t e = prepare<G, J>();
     if (e != cudaSuccess)
         return e;
-    constexpr int rows_per_cta = kWarps * (32 / G);
-    const int64_t need = (a.rows + rows_per_cta - 1) / rows_per_cta;
-    const int64_t cap = (int64_t)Cfg<G, J>::blocks_per_sm * Cfg<G, J>::sms;
-    const int grid = (int)(need < cap ? need : cap);
+    const int grid = nnls_grid(a.rows, 32 / G, Cfg<G, J>::sms, Cfg<G, J>::blocks_per_sm);
     if (grid < 1)
         return cudaSuccess;
     // an ordinary launch: started early beside the tensor-core kernel's tail
@@ -551,5 +644,6 @@ cudaError_t dispatch(const NnlsArgs &a, int G, bool prep_only, cudaStream_t s)
 cudaError_t nnls_dispatch_j2(const NnlsArgs &a, int G, bool prep_only, cudaStream_t s);
 cudaError_t nnls_dispatch_j4(const NnlsArgs &a, int G, bool prep_only, cudaStream_t s);
 cudaError_t nnls_dispatch_j8(const NnlsArgs &a, int G, bool prep_only, cudaStream_t s);
+cudaError_t nnls_dispatch_j16(const NnlsArgs &a, int G, bool prep_only, cudaStream_t s);
 
 }  // namespace nmfi

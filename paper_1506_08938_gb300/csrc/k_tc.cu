@@ -44,6 +44,7 @@ constexpr int kEpi = 256;         // threads of warps 2..9
 constexpr int kSplit = 128;       // TF32X3: warps 2..5 split, warps 6..9 accumulate
 constexpr uint32_t kABytes = 128 * 128;   // 128 rows x 128 bytes
 constexpr unsigned long long kDeadlineNs = 2000000000ull;   // 2 s, a kernel takes < 1 ms
+constexpr int kBarBytes = 1024;   // mbarriers, the TMEM address and the abort flag
 
 __device__ __forceinline__ uint32_t su32(const void *p)
 {
@@ -195,6 +196,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 32 columns of this warp's 32 TMEM lanes; the values are valid after
+// tmem_wait_ld (several loads may be in flight before one wait)
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *v)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // nearest TF32 value (10-bit mantissa): the tensor core then sees exactly
 // this value whatever rounding its own conversion uses
 __host__ __device__ __forceinline__ float rn_tf32(float v)
@@ -217,6 +236,25 @@ __host__ __device__ inline int owner_of(int64_t x, int64_t iters, int grid)
         --c;
     return (int)c;
 }
+
+constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+constexpr int lcm_c(int a, int b) { return a / gcd_c(a, b) * b; }
+
+// one k block's position in every ring of the cross kernel: data stage and
+// parity, full barrier and parity, low-part slot and parity, low-part full
+// barrier and parity, place in the issue window and the window's issuer
+struct Ring {
+    int stage = 0;
+    uint32_t phase = 0;
+    int fb = 0;
+    uint32_t fph = 0;
+    int lo = 0;
+    uint32_t lph = 0;
+    int lf = 0;
+    uint32_t lfph = 0;
+    int dc = 0;
+    int own = 0;
+};
 
 template <int MODE, int NPAD, int STAGES, int NLO, int DRAIN>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -246,6 +284,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                                    TMEM_USED <= 128 ? 128 : TMEM_USED <= 256 ? 256 : 512;
     constexpr uint32_t ID_B = idesc(MODE == TC_BF16 ? 1u : 2u, 128, NB);     // A x packed tile
     constexpr uint32_t ID_HI = idesc(2u, 128, NPAD);                         // A_lo x B_hi
+    // Issuer q owns the k blocks of every NISS-th window of DRAIN consecutive
+    // blocks of this CTA (windows are cut at row-tile boundaries into
+    // chunks).  An mbarrier wait only tells two consecutive phases apart, so
+    // every phase of a barrier must be waited by a thread that waited the one
+    // before: the full barriers (NF of them) and the low-part full barriers
+    // (NLF) are indexed so that each is only ever waited by one issuer (and
+    // by the split warps, which wait every k block in order).
+    constexpr int NF = lcm_c(STAGES, DRAIN * NISS);
+    constexpr int NLF = NLO > 0 ? lcm_c(NLO, NISS) : 1;
+    static_assert(!X3 || DRAIN == 1, "the low-part ring assumes one k block per chunk");
+    static_assert((NF + STAGES + NLF + (NLO > 0 ? NLO : 1) + 2 * NACC + 3) * 8 + 8 <= kBarBytes,
+                  "barrier area");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -254,8 +304,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto B = [&](int s) { return smem + s * STAGE_BYTES + kABytes; };
     auto LO = [&](int j) { return smem + STAGES * STAGE_BYTES + j * kABytes; };
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES + NLO * kABytes);
-    uint64_t *full = bars, *empty = bars + STAGES;
-    uint64_t *lo_full = bars + 2 * STAGES, *lo_empty = lo_full + (NLO > 0 ? NLO : 1);
+    uint64_t *full = bars, *empty = bars + NF;
+    uint64_t *lo_full = empty + STAGES, *lo_empty = lo_full + NLF;
     uint64_t *acc_full = lo_empty + (NLO > 0 ? NLO : 1), *acc_empty = acc_full + NACC;
     uint64_t *fin = acc_empty + NACC;   // every MMA of issuer q has completed: fin[q]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 3);
@@ -269,16 +319,42 @@ __global__ void __launch_bounds__(kThreads, 1)
     // 64-bit division per iteration would sit on the single-thread paths)
     const int tile0 = (int)(it0 / KB), kb0 = (int)(it0 - (int64_t)tile0 * KB);
     const unsigned long long deadline = gtimer() + kDeadlineNs;
+    // every role walks every k block of the CTA through all rings in step
+    auto adv = [](Ring &w) {
+        if (++w.stage == STAGES) {
+            w.stage = 0;
+            w.phase ^= 1u;
+        }
+        if (++w.fb == NF) {
+            w.fb = 0;
+            w.fph ^= 1u;
+        }
+        if constexpr (NLO > 0) {
+            if (++w.lo == NLO) {
+                w.lo = 0;
+                w.lph ^= 1u;
+            }
+            if (++w.lf == NLF) {
+                w.lf = 0;
+                w.lfph ^= 1u;
+            }
+        }
+        if (++w.dc == DRAIN) {
+            w.dc = 0;
+            if (++w.own == NISS)
+                w.own = 0;
+        }
+    };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NF; ++s)
             mbar_init(&full[s], 1);
+        for (int s = 0; s < STAGES; ++s)
             mbar_init(&empty[s], 1);
-        }
-        for (int j = 0; j < NLO; ++j) {
+        for (int j = 0; j < NLF; ++j)
             mbar_init(&lo_full[j], SPLIT_T);
+        for (int j = 0; j < NLO; ++j)
             mbar_init(&lo_empty[j], 1);
-        }
         for (int q = 0; q < 3; ++q)
             mbar_init(&fin[q], 1);
         for (int b = 0; b < NACC; ++b) {
@@ -321,106 +397,87 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             pdl_wait();
-            int stage = 0;
-            uint32_t phase = 0;
+            Ring w{};
             int tile = tile0, kb = kb0 - 1;
-            for (int64_t it = it0; it < it1; ++it) {
+            int64_t n = 0;   // positions whose loads were issued
+            for (int64_t it = it0; it < it1; ++it, adv(w)) {
                 if (++kb == KB) {
                     kb = 0;
                     ++tile;
                 }
                 if (it - it0 >= pre) {
-                    if (!mbar_wait(&empty[stage], phase ^ 1u, deadline, abort_flag))
+                    if (!mbar_wait(&empty[w.stage], w.phase ^ 1u, deadline, abort_flag))
                         break;
-                    mbar_expect_tx(&full[stage], TX_BYTES);
-                    tma_load_2d(A(stage), &tmA, &full[stage], kb * KSTEP_ELEMS, tile * 128);
+                    mbar_expect_tx(&full[w.fb], TX_BYTES);
+                    tma_load_2d(A(w.stage), &tmA, &full[w.fb], kb * KSTEP_ELEMS, tile * 128);
                 }
-                tma_load_2d(B(stage), &tmB, &full[stage], kb * KSTEP_ELEMS, 0);
-                if (++stage == STAGES) {
-                    stage = 0;
-                    phase ^= 1u;
-                }
+                tma_load_2d(B(w.stage), &tmB, &full[w.fb], kb * KSTEP_ELEMS, 0);
+                n = it - it0 + 1;
             }
-            // drain: every load issued must land before the CTA exits
-            for (int s = 0; s < STAGES; ++s) {
-                if (!mbar_wait(&empty[stage], phase ^ 1u, deadline + kDeadlineNs, abort_flag)) {
+            // drain: every load issued must land before the CTA exits; the
+            // last use of the slot at position n + s was position n + s - STAGES
+            for (int s = 0; s < STAGES; ++s, adv(w)) {
+                const int64_t last = n + s - STAGES;
+                if (!mbar_wait(&empty[w.stage], w.phase ^ 1u, deadline + kDeadlineNs, abort_flag) &&
+                    last >= 0) {
                     // the consumer stopped; wait for the load itself instead
-                    mbar_wait_drain(&full[stage], phase, deadline + 2 * kDeadlineNs);
-                }
-                if (++stage == STAGES) {
-                    stage = 0;
-                    phase ^= 1u;
+                    mbar_wait_drain(&full[last % NF], (uint32_t)((last / NF) & 1),
+                                    deadline + 2 * kDeadlineNs);
                 }
             }
         }
     } else if (warp == kIssuer0 || warp == kIssuer1 || warp == kIssuer2) {
-        // ---------------- MMA issuers: issuer q takes the accumulation chunks
-        // c with c % NISS == q, so one thread's barrier waits and commits
-        // overlap the others' MMAs.  Chunk c accumulates in buffer c % NACC
-        // (NACC == NISS), which only its issuer touches; stage and low-part
-        // reuse stay ordered through the producer and split barriers, and
-        // tcgen05.commit tracks the MMAs of the thread that issues it.
+        // ---------------- MMA issuers: issuer q takes the k blocks of the
+        // windows w with w % NISS == q and accumulates them in buffer q, which
+        // only it touches, so one thread's barrier waits and commits overlap
+        // the others' MMAs; stage and low-part reuse stay ordered through the
+        // producer and split barriers, and tcgen05.commit tracks the MMAs of
+        // the thread that issues it.
         const int q = warp == kIssuer0 ? 0 : (warp == kIssuer1 ? 1 : 2);
         if (lane == 0 && q < NISS) {
-            int stage = 0, buf = 0, pos = 0, lo = 0, chunk = -1;
-            uint32_t phase = 0, lo_phase = 0, uses[NACC] = {};
+            Ring w{};
+            uint32_t uses = 0;
+            const uint32_t d = tmem + q * BUF_COLS;
             int kb = kb0 - 1;
-            for (int64_t it = it0; it < it1; ++it) {
+            for (int64_t it = it0; it < it1; ++it, adv(w)) {
                 if (++kb == KB)
                     kb = 0;
+                if (w.own != q)
+                    continue;
                 const bool seg_start = it == it0 || kb == 0;
                 const bool seg_end = it + 1 == it1 || kb == KB - 1;
-                pos = seg_start ? 0 : pos + 1;
-                const bool chunk_start = pos % DRAIN == 0;
-                const bool chunk_end = seg_end || pos % DRAIN == DRAIN - 1;
-                if (chunk_start)
-                    ++chunk;
-                if (chunk % NISS == q) {
-                    if (chunk_start) {
-                        // the accumulating warps have drained the previous use of this buffer
-                        const uint32_t u = uses[buf]++;
-                        if (!mbar_wait(&acc_empty[buf], (u & 1u) ^ 1u, deadline, abort_flag))
-                            break;
-                        tc_fence_after();
-                    }
-                    if (!mbar_wait(&full[stage], phase, deadline, abort_flag))
+                const bool chunk_start = seg_start || w.dc == 0;
+                const bool chunk_end = seg_end || w.dc == DRAIN - 1;
+                if (chunk_start) {
+                    // the accumulating warps have drained the previous use of this buffer
+                    const uint32_t u = uses++;
+                    if (!mbar_wait(&acc_empty[q], (u & 1u) ^ 1u, deadline, abort_flag))
                         break;
                     tc_fence_after();
-                    const uint32_t d = tmem + buf * BUF_COLS;
-                    const uint32_t a0 = su32(A(stage)), b0 = su32(B(stage));
-                    // X3: columns [0, NPAD) get A B_hi, columns [NPAD, 2 NPAD) get
-                    // A B_lo; these need no low part, so they run while the split finishes
-#pragma unroll
-                    for (int kk = 0; kk < KMMA; ++kk)
-                        mma<MODE>(d, sdesc(a0 + 32 * kk), sdesc(b0 + 32 * kk), ID_B,
-                                  (chunk_start && kk == 0) ? 0u : 1u);
-                    if constexpr (X3) {
-                        if (!mbar_wait(&lo_full[lo], lo_phase, deadline, abort_flag))
-                            break;   // the final commit below waits for the MMAs issued
-                        tc_fence_after();
-                        const uint32_t l0 = su32(LO(lo));
-#pragma unroll
-                        for (int kk = 0; kk < KMMA; ++kk)   // A_lo x B_hi (first NPAD rows)
-                            mma<MODE>(d, sdesc(l0 + 32 * kk), sdesc(b0 + 32 * kk), ID_HI, 1u);
-                        mma_commit(&lo_empty[lo]);
-                    }
-                    mma_commit(&empty[stage]);
-                    if (chunk_end)
-                        mma_commit(&acc_full[buf]);
                 }
-                // every issuer walks every k block's ring positions
+                if (!mbar_wait(&full[w.fb], w.fph, deadline, abort_flag))
+                    break;
+                tc_fence_after();
+                const uint32_t a0 = su32(A(w.stage)), b0 = su32(B(w.stage));
+                // X3: columns [0, NPAD) get A B_hi, columns [NPAD, 2 NPAD) get
+                // A B_lo; these need no low part, so they run while the split finishes
+#pragma unroll
+                for (int kk = 0; kk < KMMA; ++kk)
+                    mma<MODE>(d, sdesc(a0 + 32 * kk), sdesc(b0 + 32 * kk), ID_B,
+                              (chunk_start && kk == 0) ? 0u : 1u);
                 if constexpr (X3) {
-                    if (++lo == NLO) {
-                        lo = 0;
-                        lo_phase ^= 1u;
-                    }
+                    if (!mbar_wait(&lo_full[w.lf], w.lfph, deadline, abort_flag))
+                        break;   // the final commit below waits for the MMAs issued
+                    tc_fence_after();
+                    const uint32_t l0 = su32(LO(w.lo));
+#pragma unroll
+                    for (int kk = 0; kk < KMMA; ++kk)   // A_lo x B_hi (first NPAD rows)
+                        mma<MODE>(d, sdesc(l0 + 32 * kk), sdesc(b0 + 32 * kk), ID_HI, 1u);
+                    mma_commit(&lo_empty[w.lo]);
                 }
-                if (chunk_end && ++buf == NACC)
-                    buf = 0;
-                if (++stage == STAGES) {
-                    stage = 0;
-                    phase ^= 1u;
-                }
+                mma_commit(&empty[w.stage]);
+                if (chunk_end)
+                    mma_commit(&acc_full[q]);
             }
             // however the loop ended, no MMA may still write TMEM when it is freed
             mma_commit(&fin[q]);
@@ -433,17 +490,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         // rounded to TF32, is written to the low ring.  The MMA of a stage
         // waits for its low part, so the stage (and A in it) stays valid here.
         const int t = threadIdx.x - 64;   // 0..127
-        int stage = 0, lo = 0;
-        uint32_t phase = 0, lo_phase = 0;
-        for (int64_t it = it0; it < it1; ++it) {
+        Ring w{};
+        for (int64_t it = it0; it < it1; ++it, adv(w)) {
             // warp-uniform decisions: every lane of the warp continues or none
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, deadline, abort_flag)))
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[w.fb], w.fph, deadline, abort_flag)))
                 break;
             if (!__all_sync(0xffffffffu,
-                            mbar_wait(&lo_empty[lo], lo_phase ^ 1u, deadline, abort_flag)))
+                            mbar_wait(&lo_empty[w.lo], w.lph ^ 1u, deadline, abort_flag)))
                 break;
-            const float4 *a4 = reinterpret_cast<const float4 *>(A(stage));
-            float4 *l4 = reinterpret_cast<float4 *>(LO(lo));
+            const float4 *a4 = reinterpret_cast<const float4 *>(A(w.stage));
+            float4 *l4 = reinterpret_cast<float4 *>(LO(w.lo));
             float4 v[kABytes / 16 / kSplit];
 #pragma unroll
             for (int q = 0; q < (int)(kABytes / 16 / kSplit); ++q)
@@ -458,15 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 l4[t + kSplit * q] = r;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(&lo_full[lo]);
-            if (++lo == NLO) {
-                lo = 0;
-                lo_phase ^= 1u;
-            }
-            if (++stage == STAGES) {
-                stage = 0;
-                phase ^= 1u;
-            }
+            mbar_arrive(&lo_full[w.lf]);
         }
     } else {
         // ---------------- accumulation: warps 6..9 (SR) or 2..9
@@ -484,14 +532,23 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < HC; ++j)
             acc[j] = 0.f;
-        int buf = 0, pos = 0, pending = -1;
+        int pending = -1;
         uint32_t drains[NACC] = {};
-        int stage = 0, lo = 0;                       // inline split (X3 without SR)
-        uint32_t phase = 0, lo_phase = 0;
+        Ring w{};
         const int t = threadIdx.x - 64;
         bool ok = true;
         auto ld_add = [&](uint32_t addr) {
-            if constexpr (HC >= 16) {
+            if constexpr (HC % 32 == 0) {
+                // every load of the region in flight before one wait
+                uint32_t v[HC];
+#pragma unroll
+                for (int c0 = 0; c0 < HC; c0 += 32)
+                    tmem_ld32_nowait(addr + c0, v + c0);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < HC; ++j)
+                    acc[j] += __uint_as_float(v[j]);
+            } else if constexpr (HC >= 16) {
 #pragma unroll
                 for (int c0 = 0; c0 < HC; c0 += 16) {
                     uint32_t v[16];
@@ -523,24 +580,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             return true;
         };
         int tile = tile0, kb = kb0 - 1;
-        for (int64_t it = it0; it < it1 && ok; ++it) {
+        for (int64_t it = it0; it < it1 && ok; ++it, adv(w)) {
             if (++kb == KB) {
                 kb = 0;
                 ++tile;
             }
-            const bool seg_start = it == it0 || kb == 0;
             const bool seg_end = it + 1 == it1 || kb == KB - 1;
-            pos = seg_start ? 0 : pos + 1;
-            const bool chunk_end = seg_end || pos % DRAIN == DRAIN - 1;
+            const bool chunk_end = seg_end || w.dc == DRAIN - 1;
             if constexpr (X3 && !SR) {
                 // split this stage first (same step as the split warps above)
-                if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, deadline, abort_flag)))
+                if (!__all_sync(0xffffffffu, mbar_wait(&full[w.fb], w.fph, deadline, abort_flag)))
                     break;
                 if (!__all_sync(0xffffffffu,
-                                mbar_wait(&lo_empty[lo], lo_phase ^ 1u, deadline, abort_flag)))
+                                mbar_wait(&lo_empty[w.lo], w.lph ^ 1u, deadline, abort_flag)))
                     break;
-                const float4 *a4 = reinterpret_cast<const float4 *>(A(stage));
-                float4 *l4 = reinterpret_cast<float4 *>(LO(lo));
+                const float4 *a4 = reinterpret_cast<const float4 *>(A(w.stage));
+                float4 *l4 = reinterpret_cast<float4 *>(LO(w.lo));
 #pragma unroll
                 for (int q = 0; q < (int)(kABytes / 16 / kEpi); ++q) {
                     const float4 v = a4[t + kEpi * q];
@@ -552,15 +607,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     l4[t + kEpi * q] = r;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(&lo_full[lo]);
-                if (++lo == NLO) {
-                    lo = 0;
-                    lo_phase ^= 1u;
-                }
-                if (++stage == STAGES) {
-                    stage = 0;
-                    phase ^= 1u;
-                }
+                mbar_arrive(&lo_full[w.lf]);
             }
             // drain the previous chunk now that the tensor core has the next one
             if (pending >= 0) {
@@ -571,9 +618,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!chunk_end)
                 continue;
-            const int b = buf;
-            if (++buf == NACC)
-                buf = 0;
+            const int b = w.own;   // the issuer of this window accumulates in its buffer
             if (!seg_end) {
                 pending = b;
                 continue;
@@ -695,11 +740,13 @@ struct TcCfg {
     static constexpr int NLO = MODE == TC_TF32X3 ? 3 : 0;       // low-part ring
     static constexpr int NB = MODE == TC_TF32X3 ? 2 * NPAD : NPAD;
     static constexpr int STAGE = kABytes + NB * 128;
+    // as many stages as fit: A in flight from HBM is what the ring buys
     static constexpr int ST0 = (220 * 1024 - NLO * (int)kABytes) / STAGE;
     static constexpr int STAGES = ST0 > 8 ? 8 : ST0;
     static constexpr int DRAIN = MODE == TC_TF32X3 ? 1 : 2;     // k blocks per chunk
-    // + 1024 for the 1024-byte alignment of the tiles, + 512 for the barriers
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE + (size_t)NLO * kABytes + 1024 + 512;
+    // + 1024 for the 1024-byte alignment of the tiles, + the barrier area
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE + (size_t)NLO * kABytes + 1024 + kBarBytes;
+    static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
 };
 
 template <int MODE, int NPAD>

@@ -145,14 +145,13 @@ def test_nnls_converges_to_unique_minimiser(h, r):
 
 def layouts(r):
     """Every lanes-per-row setting the solver accepts for rank r."""
-    return [g for g in (1, 2, 4, 8, 16, 32) if g * 8 >= r]
+    return [g for g in (1, 2, 4, 8, 16, 32) if g * 16 >= r]
 
 
 @pytest.mark.parametrize("r", [2, 3, 9, 17, 33, 50, 64, 100, 128])
 def test_nnls_every_layout(h, r):
     """Each group width (lanes per row) and coordinates-per-lane split: the
-    unique minimiser within the FP32 bound, fixed-K iterates row by row; rows
-    more than the warps of one wave, so groups take several rows each."""
+    unique minimiser within the FP32 bound, fixed-K iterates row by row."""
     rows = 3 * 8 * 32 + 11
     Q, Cm, X0 = nqp_batch(700 + r, r, rows, beta=0.1)
     tol = nnls_tol(Q, r)
@@ -166,10 +165,30 @@ def test_nnls_every_layout(h, r):
         assert np.all(it <= 3)
 
 
+@pytest.mark.parametrize("lanes", [0, 4])
+def test_nnls_rows_independent_of_launch(h, lanes):
+    """A row's result depends on r and the layout only, not on the rows that
+    share its launch: one launch over 20000 rows (balanced CTA ranges, two
+    rounds for some warps) equals, bit for bit, launches over uneven
+    sub-ranges; the one-launch result is checked against the oracle's fixed-K
+    iterates on a sample of rows."""
+    r, rows, K = 50, 20000, 3
+    Q, Cm, X0 = nqp_batch(808, r, rows, beta=0.1)
+    opts = P.nnls_opts(max_inner=K, eps=0.0, lanes=lanes)
+    X, it = gpu_nnls(h, Q, Cm, X0, 0.01, opts)
+    cuts = [0, 1, 37, 4133, 9000, 19999, 20000]
+    parts = [gpu_nnls(h, Q, Cm[lo:hi], X0[lo:hi], 0.01, opts) for lo, hi in zip(cuts, cuts[1:])]
+    assert np.array_equal(X, np.concatenate([p[0] for p in parts]))
+    assert np.array_equal(it, np.concatenate([p[1] for p in parts]))
+    sample = np.r_[0:40, 9990:10010, 19960:20000]
+    Xk, *_ = O.nnls_update(Q, Cm[sample], 0.01, X0[sample], O.nqp_opts(max_inner=K, eps=0.0))
+    assert_fixed_k_rows(X[sample], Xk, Q, Cm[sample], 0.01, nnls_tol(Q, r))
+
+
 def test_nnls_layout_rejects_too_few_lanes(h):
     Q, Cm, X0 = nqp_batch(5, 50, 10)
     with pytest.raises(P.NmfError):
-        gpu_nnls(h, Q, Cm, X0, 0.0, P.nnls_opts(lanes=4))    # 4 lanes x 8 < 50
+        gpu_nnls(h, Q, Cm, X0, 0.0, P.nnls_opts(lanes=2))    # 2 lanes x 16 < 50
     with pytest.raises(P.NmfError):
         gpu_nnls(h, Q, Cm, X0, 0.0, P.nnls_opts(lanes=3))    # not a power of two
 
