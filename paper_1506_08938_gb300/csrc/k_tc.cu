@@ -214,6 +214,33 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *v)
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 32 columns of this warp's 32 TMEM lanes from registers; visible to later
+// tcgen05 operations after tmem_wait_st and a thread-sync fence
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+        "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),
+        "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),
+        "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D (+)= A B with A (M x 8, TF32) in tensor memory and B in shared memory
+__device__ __forceinline__ void mma_tf32_atmem(uint32_t d, uint32_t a, uint64_t b, uint32_t id,
+                                               uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a), "l"(b), "r"(id), "r"(acc));
+}
+
 // nearest TF32 value (10-bit mantissa): the tensor core then sees exactly
 // this value whatever rounding its own conversion uses
 __host__ __device__ __forceinline__ float rn_tf32(float v)
@@ -279,7 +306,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     // chunks; three issuers where three buffers fit in TMEM's 512 columns
     constexpr int NISS = 512 / BUF_COLS >= 3 ? 3 : 2;
     constexpr int NACC = NISS == 3 ? 3 : 2;
-    constexpr uint32_t TMEM_USED = NACC * BUF_COLS;
+    // SR: the low parts live in tensor memory (32 columns per k block, one
+    // lane per row), read by the A_lo MMAs from there: no shared-memory
+    // round trip for them
+    constexpr uint32_t LO_COL0 = NACC * BUF_COLS;
+    constexpr uint32_t TMEM_USED = NACC * BUF_COLS + (SR ? NLO * 32 : 0);
+    static_assert(TMEM_USED <= 512, "tensor memory columns");
     constexpr uint32_t TMEM_COLS = TMEM_USED <= 32 ? 32 : TMEM_USED <= 64 ? 64 :
                                    TMEM_USED <= 128 ? 128 : TMEM_USED <= 256 ? 256 : 512;
     constexpr uint32_t ID_B = idesc(MODE == TC_BF16 ? 1u : 2u, 128, NB);     // A x packed tile
@@ -302,8 +334,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                 ~uintptr_t(1023));
     auto A = [&](int s) { return smem + s * STAGE_BYTES; };
     auto B = [&](int s) { return smem + s * STAGE_BYTES + kABytes; };
+    // the shared-memory low-part ring (NPAD 128 only; SR keeps it in TMEM)
+    constexpr int NLO_SM = SR ? 0 : NLO;
     auto LO = [&](int j) { return smem + STAGES * STAGE_BYTES + j * kABytes; };
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES + NLO * kABytes);
+    // epilogue staging: 8 rows x NPAD floats per TMEM lane quadrant
+    float *stg_all = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + NLO_SM * kABytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stg_all + 4 * 8 * NPAD);
     uint64_t *full = bars, *empty = bars + NF;
     uint64_t *lo_full = empty + STAGES, *lo_empty = lo_full + NLF;
     uint64_t *acc_full = lo_empty + (NLO > 0 ? NLO : 1), *acc_empty = acc_full + NACC;
@@ -469,10 +505,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!mbar_wait(&lo_full[w.lf], w.lfph, deadline, abort_flag))
                         break;   // the final commit below waits for the MMAs issued
                     tc_fence_after();
-                    const uint32_t l0 = su32(LO(w.lo));
+                    if constexpr (SR) {
+                        const uint32_t l0 = tmem + LO_COL0 + w.lo * 32;
 #pragma unroll
-                    for (int kk = 0; kk < KMMA; ++kk)   // A_lo x B_hi (first NPAD rows)
-                        mma<MODE>(d, sdesc(l0 + 32 * kk), sdesc(b0 + 32 * kk), ID_HI, 1u);
+                        for (int kk = 0; kk < KMMA; ++kk)   // A_lo x B_hi (first NPAD rows)
+                            mma_tf32_atmem(d, l0 + 8 * kk, sdesc(b0 + 32 * kk), ID_HI, 1u);
+                    } else {
+                        const uint32_t l0 = su32(LO(w.lo));
+#pragma unroll
+                        for (int kk = 0; kk < KMMA; ++kk)   // A_lo x B_hi (first NPAD rows)
+                            mma<MODE>(d, sdesc(l0 + 32 * kk), sdesc(b0 + 32 * kk), ID_HI, 1u);
+                    }
                     mma_commit(&lo_empty[w.lo]);
                 }
                 mma_commit(&empty[w.stage]);
@@ -487,9 +530,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- TF32X3 split: warps 2..5, 128 threads.  The tensor
         // core reads A through its TF32 conversion, which truncates, so A
         // itself acts as the high part and the remainder A - trunc(A),
-        // rounded to TF32, is written to the low ring.  The MMA of a stage
-        // waits for its low part, so the stage (and A in it) stays valid here.
-        const int t = threadIdx.x - 64;   // 0..127
+        // rounded to TF32, goes to the low ring in tensor memory: the thread
+        // of TMEM lane `row` reads row `row` of the 128B-swizzled A tile (its
+        // 16-byte chunk c sits at chunk c ^ (row mod 8)) and stores its 32
+        // low parts along that lane.  The MMA of a stage waits for its low
+        // part, so the stage (and A in it) stays valid here.
+        const int quad = warp & 3;               // TMEM lane quadrant of this warp
+        const int row = quad * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
         Ring w{};
         for (int64_t it = it0; it < it1; ++it, adv(w)) {
             // warp-uniform decisions: every lane of the warp continues or none
@@ -498,22 +546,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!__all_sync(0xffffffffu,
                             mbar_wait(&lo_empty[w.lo], w.lph ^ 1u, deadline, abort_flag)))
                 break;
-            const float4 *a4 = reinterpret_cast<const float4 *>(A(w.stage));
-            float4 *l4 = reinterpret_cast<float4 *>(LO(w.lo));
-            float4 v[kABytes / 16 / kSplit];
+            tc_fence_after();
+            const uint8_t *ar = A(w.stage) + row * 128;
+            uint32_t r[32];
 #pragma unroll
-            for (int q = 0; q < (int)(kABytes / 16 / kSplit); ++q)
-                v[q] = a4[t + kSplit * q];
-#pragma unroll
-            for (int q = 0; q < (int)(kABytes / 16 / kSplit); ++q) {
-                float4 r;
-                r.x = rn_tf32(v[q].x - __uint_as_float(__float_as_uint(v[q].x) & 0xffffe000u));
-                r.y = rn_tf32(v[q].y - __uint_as_float(__float_as_uint(v[q].y) & 0xffffe000u));
-                r.z = rn_tf32(v[q].z - __uint_as_float(__float_as_uint(v[q].z) & 0xffffe000u));
-                r.w = rn_tf32(v[q].w - __uint_as_float(__float_as_uint(v[q].w) & 0xffffe000u));
-                l4[t + kSplit * q] = r;
+            for (int c = 0; c < 8; ++c) {
+                const float4 v = *reinterpret_cast<const float4 *>(ar + 16 * (c ^ (row & 7)));
+                r[4 * c + 0] = __float_as_uint(rn_tf32(v.x - __uint_as_float(__float_as_uint(v.x) & 0xffffe000u)));
+                r[4 * c + 1] = __float_as_uint(rn_tf32(v.y - __uint_as_float(__float_as_uint(v.y) & 0xffffe000u)));
+                r[4 * c + 2] = __float_as_uint(rn_tf32(v.z - __uint_as_float(__float_as_uint(v.z) & 0xffffe000u)));
+                r[4 * c + 3] = __float_as_uint(rn_tf32(v.w - __uint_as_float(__float_as_uint(v.w) & 0xffffe000u)));
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tmem_st32(tmem + lane_addr + LO_COL0 + w.lo * 32, r);
+            tmem_wait_st();
+            tc_fence_before();
             mbar_arrive(&lo_full[w.lf]);
         }
     } else {
@@ -630,20 +676,46 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int c_first = owner_of(first_it, p.iters, p.grid);
             const int c_last = owner_of(last_it, p.iters, p.grid);
             const int slice = (int)blockIdx.x - c_first;
-            const int64_t row = (int64_t)tile * 128 + quad * 32 + lane;
-            if (row < p.M) {
-                float *dst = p.P + (int64_t)slice * p.M * p.r + row * p.r + half * HC;
+            // The rows of this quadrant form one contiguous run of the slice
+            // (rows of r floats).  Groups of 8 rows go through shared memory
+            // and out with consecutive threads on consecutive floats: a row
+            // per thread straight to global memory would cost a separate
+            // memory transaction for every lane of every store.
+            const int r = p.r;
+            const int64_t row0 = (int64_t)tile * 128 + quad * 32;
+            const int64_t left = p.M - row0;
+            const int nrow = left <= 0 ? 0 : (left < 32 ? (int)left : 32);
+            constexpr int QT = SR ? 32 : 64;                  // threads of a quadrant
+            const int qt = SR ? lane : half * 32 + lane;
+            float *stg = stg_all + quad * 8 * NPAD;
+            auto qsync = [&]() {
+                if constexpr (SR)
+                    __syncwarp();
+                else
+                    asm volatile("bar.sync %0, 64;" ::"r"(1 + quad) : "memory");
+            };
+            float *dst = p.P + (int64_t)slice * p.M * r + row0 * r;
+            for (int g = 0; g < nrow; g += 8) {
+                const int nr = nrow - g < 8 ? nrow - g : 8;
+                if (lane >= g && lane < g + nr) {
+                    float *sr = stg + (lane - g) * r + half * HC;
 #pragma unroll
-                for (int j = 0; j < HC; ++j)
-                    if (half * HC + j < p.r)
-                        dst[j] = acc[j];
-                // the first part of a tile clears the slices no CTA writes for it
-                if (slice == 0) {
-                    for (int s2 = c_last - c_first + 1; s2 < p.nslices; ++s2) {
-                        float *z = p.P + (int64_t)s2 * p.M * p.r + row * p.r + half * HC;
-                        for (int j = 0; j < HC && half * HC + j < p.r; ++j)
-                            z[j] = 0.f;
-                    }
+                    for (int j = 0; j < HC; ++j)
+                        if (half * HC + j < r)
+                            sr[j] = acc[j];
+                }
+                qsync();
+                float *d = dst + (int64_t)g * r;
+                for (int e = qt; e < nr * r; e += QT)
+                    d[e] = stg[e];
+                qsync();
+            }
+            // the first part of a tile clears the slices no CTA writes for it
+            if (slice == 0) {
+                for (int s2 = c_last - c_first + 1; s2 < p.nslices; ++s2) {
+                    float *z = p.P + (int64_t)s2 * p.M * r + row0 * r;
+                    for (int e = qt; e < nrow * r; e += QT)
+                        z[e] = 0.f;
                 }
             }
 #pragma unroll
@@ -738,14 +810,19 @@ bool make_map(CUtensorMap *m, const void *base, bool bf16, uint64_t inner, uint6
 template <int MODE, int NPAD>
 struct TcCfg {
     static constexpr int NLO = MODE == TC_TF32X3 ? 3 : 0;       // low-part ring
+    // its shared-memory copy: only without the split warps (NPAD 128); with
+    // them (NPAD <= 64) the ring is in tensor memory
+    static constexpr int NLO_SM = MODE == TC_TF32X3 && NPAD > 64 ? NLO : 0;
     static constexpr int NB = MODE == TC_TF32X3 ? 2 * NPAD : NPAD;
     static constexpr int STAGE = kABytes + NB * 128;
     // as many stages as fit: A in flight from HBM is what the ring buys
-    static constexpr int ST0 = (220 * 1024 - NLO * (int)kABytes) / STAGE;
+    static constexpr int STG = 4 * 8 * NPAD * 4;                // epilogue staging bytes
+    static constexpr int ST0 = (220 * 1024 - NLO_SM * (int)kABytes - STG) / STAGE;
     static constexpr int STAGES = ST0 > 8 ? 8 : ST0;
     static constexpr int DRAIN = MODE == TC_TF32X3 ? 1 : 2;     // k blocks per chunk
     // + 1024 for the 1024-byte alignment of the tiles, + the barrier area
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE + (size_t)NLO * kABytes + 1024 + kBarBytes;
+    static constexpr size_t SMEM =
+        (size_t)STAGES * STAGE + (size_t)NLO_SM * kABytes + STG + 1024 + kBarBytes;
     static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
 };
 
