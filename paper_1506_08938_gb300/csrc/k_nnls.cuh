@@ -162,14 +162,97 @@ __device__ __forceinline__ void matvec_buf(const float *__restrict__ Qs, const f
     }
 }
 
-// stage v (a lane's J values) in the group buffer vbg, then out = Qt v
+// The products of all groups of the warp with each Qt load shared among
+// the groups: lane L computes coordinates [L CL, L CL + CL) of every group's
+// product (CL = RP / 32), then the products pass through the groups' output
+// buffers (stride VB from out0) into the coordinate-step layout.  Inputs are
+// read from in0 (group buffers, stride VB; in0 may equal out0).  Each output
+// takes its k terms in the order matvec_buf does, so the results agree bit
+// for bit; the shared loads cut the shared-memory wavefronts of a product
+// about 2.5-fold when a warp holds several groups.
 template <int G, int J>
-__device__ __forceinline__ void matvec(const float *__restrict__ Qs, float *vbg,
-                                       const float (&v)[J], float (&out)[J], int li, int r4)
+constexpr bool coop_matvec() { return 32 / G >= 2 && Map<G, J>::RP % 32 == 0; }
+
+template <int G, int J>
+__device__ __forceinline__ void matvec_coop(const float *__restrict__ Qs, const float *in0,
+                                            float *out0, float (&out)[J], int gi, int li, int r4)
+{
+    using M = Map<G, J>;
+    constexpr int RP = M::RP, NG = 32 / G, CL = RP / 32, VB = M::VB;
+    const int lane = threadIdx.x & 31;
+    float acc[NG][CL];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int i = 0; i < CL; ++i)
+            acc[g][i] = 0.f;
+    for (int k = 0; k < r4; k += 4) {
+        float4 v[NG];
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+            v[g] = *reinterpret_cast<const float4 *>(in0 + g * VB + k);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const float *qp = Qs + (k + kk) * RP + lane * CL;
+            float q[CL];
+            if constexpr (CL == 4) {
+                const float4 t = *reinterpret_cast<const float4 *>(qp);
+                q[0] = t.x; q[1] = t.y; q[2] = t.z; q[3] = t.w;
+            } else if constexpr (CL == 2) {
+                const float2 t = *reinterpret_cast<const float2 *>(qp);
+                q[0] = t.x; q[1] = t.y;
+            } else {
+                q[0] = qp[0];
+            }
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const float vk = kk == 0 ? v[g].x : kk == 1 ? v[g].y : kk == 2 ? v[g].z : v[g].w;
+#pragma unroll
+                for (int i = 0; i < CL; ++i)
+                    acc[g][i] = fmaf(q[i], vk, acc[g][i]);
+            }
+        }
+    }
+    __syncwarp();   // every lane has read its inputs
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        float *op = out0 + g * VB + lane * CL;
+        if constexpr (CL == 4)
+            *reinterpret_cast<float4 *>(op) = make_float4(acc[g][0], acc[g][1], acc[g][2], acc[g][3]);
+        else if constexpr (CL == 2)
+            *reinterpret_cast<float2 *>(op) = make_float2(acc[g][0], acc[g][1]);
+        else
+            op[0] = acc[g][0];
+    }
+    __syncwarp();
+    ld_lane<G, J>(out0 + gi * VB, li, out);
+    __syncwarp();   // the buffers may be rewritten next
+}
+
+// out = Qt v for this lane's group, v in the group buffer vg (the warp's
+// group buffers start at v0); products land in the warp's buffers at out0
+// when the groups share the loads
+template <int G, int J>
+__device__ __forceinline__ void matvec_rows(const float *__restrict__ Qs, const float *v0,
+                                            const float *vg, float *out0, float (&out)[J],
+                                            int gi, int li, int r4)
+{
+    if constexpr (coop_matvec<G, J>())
+        matvec_coop<G, J>(Qs, v0, out0, out, gi, li, r4);
+    else
+        matvec_buf<G, J>(Qs, vg, out, li, r4);
+}
+
+// stage v (a lane's J values) in the group buffer vbg, then out = Qt v
+// (vb0: the warp's first group buffer)
+template <int G, int J>
+__device__ __forceinline__ void matvec(const float *__restrict__ Qs, float *vb0, float *vbg,
+                                       const float (&v)[J], float (&out)[J], int gi, int li,
+                                       int r4)
 {
     st_lane<G, J>(vbg, li, v);
     __syncwarp();
-    matvec_buf<G, J>(Qs, vbg, out, li, r4);
+    matvec_rows<G, J>(Qs, vb0, vbg, vb0, out, gi, li, r4);
     __syncwarp();
 }
 
@@ -257,8 +340,9 @@ __device__ __forceinline__ uint2 nnls_rows(const NnlsArgs &a, const float *__res
     constexpr int NG = 32 / G;            // rows per warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gi = lane / G, li = lane - gi * G;
-    float *vbg = pool + (warp * NG + gi) * M::VB;                        // staging
-    float *ysg = pool + (kWarps * NG + warp * NG + gi) * M::VB;          // iterate y
+    float *vb0 = pool + warp * NG * M::VB;                               // staging
+    float *ys0 = pool + (kWarps * NG + warp * NG) * M::VB;               // iterate y
+    float *vbg = vb0 + gi * M::VB, *ysg = ys0 + gi * M::VB;              // this group's
     const int r = a.r;
     const int r4 = (r + 3) & ~3;
 
@@ -366,7 +450,7 @@ __device__ __forceinline__ uint2 nnls_rows(const NnlsArgs &a, const float *__res
             const bool gok = group_bits<G>(__ballot_sync(kFull, ok), gi) == group_full<G>();
             __syncwarp();
             float t[J];
-            matvec_buf<G, J>(Qs, ysg, t, li, r4);   // busy groups' products are not used
+            matvec_rows<G, J>(Qs, ys0, ysg, vb0, t, gi, li, r4);   // busy groups' are unused
             __syncwarp();
             if (fresh) {
 #pragma unroll
@@ -408,7 +492,7 @@ __device__ __forceinline__ uint2 nnls_rows(const NnlsArgs &a, const float *__res
             s = group_sum<G>(s);
             if (__any_sync(kFull, s > 0.f)) {
                 float u[J];
-                matvec<G, J>(Qs, vbg, gb, u, li, r4);
+                matvec<G, J>(Qs, vb0, vbg, gb, u, gi, li, r4);
                 float den = 0.f;
 #pragma unroll
                 for (int j = 0; j < J; ++j)
@@ -422,7 +506,7 @@ __device__ __forceinline__ uint2 nnls_rows(const NnlsArgs &a, const float *__res
                     y[j] = yn;
                 }
                 st_lane<G, J>(ysg, li, y);
-                matvec<G, J>(Qs, vbg, gb, u, li, r4);
+                matvec<G, J>(Qs, vb0, vbg, gb, u, gi, li, r4);
 #pragma unroll
                 for (int j = 0; j < J; ++j)
                     g[j] += u[j];
