@@ -11,6 +11,8 @@
 //      over interleaved slices, then the warp sums in warp order: a fixed
 //      order, so the result is reproducible - and the last CTA to finish
 //      (ticket counter) rescales and clears the counter.
+// Both kernels issue their global loads in batches before using them: a
+// load whose value is stored or added right away holds the next load back.
 #include "nmf_internal.cuh"
 
 namespace nmfi {
@@ -44,10 +46,18 @@ __global__ void __launch_bounds__(kThreads) k_factor_prep(const PrepArgs a)
             acc[i][j] = 0.f;
 
     for (int64_t kb = k0; kb < k1; kb += kRowsBlock) {
-        for (int idx = tid; idx < kRowsBlock * NB; idx += kThreads) {
-            const int kk = idx / NB, c = idx - kk * NB;
+        constexpr int PER = kRowsBlock * NB / kThreads;
+        float v[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int idx = tid + q * kThreads, kk = idx / NB, c = idx % NB;
             const int64_t gk = kb + kk;
-            Xs[kk][c] = (c < r && gk < k1) ? a.X[gk * r + c] : 0.f;
+            v[q] = (c < r && gk < k1) ? a.X[gk * r + c] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int idx = tid + q * kThreads;
+            Xs[idx / NB][idx % NB] = v[q];
         }
         __syncthreads();
 #pragma unroll 4
@@ -99,6 +109,8 @@ __global__ void __launch_bounds__(kThreads) k_factor_prep(const PrepArgs a)
         }
 }
 
+constexpr int kPerWarp = (kMaxSlices + kSumWarps - 1) / kSumWarps;   // slices per warp at most
+
 // G[e] = sum_s P[s][e] for 32 consecutive e per CTA, then (last CTA) Q, Qt, d
 __global__ void __launch_bounds__(kSumWarps * 32) k_prep_finish(const PrepArgs a, int S)
 {
@@ -111,19 +123,19 @@ __global__ void __launch_bounds__(kSumWarps * 32) k_prep_finish(const PrepArgs a
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int e = blockIdx.x * 32 + lane;
     {
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        if (e < n) {
-            int k = w;
-            for (; k + 3 * kSumWarps < S; k += 4 * kSumWarps) {
-                s0 += a.P[(int64_t)k * n + e];
-                s1 += a.P[(int64_t)(k + kSumWarps) * n + e];
-                s2 += a.P[(int64_t)(k + 2 * kSumWarps) * n + e];
-                s3 += a.P[(int64_t)(k + 3 * kSumWarps) * n + e];
-            }
-            for (; k < S; k += kSumWarps)
-                s0 += a.P[(int64_t)k * n + e];
+        // this warp's slices w, w + kSumWarps, ... in order, every load
+        // issued before the first add
+        float v[kPerWarp];
+#pragma unroll
+        for (int u = 0; u < kPerWarp; ++u) {
+            const int k = w + u * kSumWarps;
+            v[u] = (e < n && k < S) ? a.P[(int64_t)k * n + e] : 0.f;
         }
-        part[w][lane] = (s0 + s1) + (s2 + s3);
+        float acc = 0.f;
+#pragma unroll
+        for (int u = 0; u < kPerWarp; ++u)
+            acc += v[u];
+        part[w][lane] = acc;
     }
     __syncthreads();
     if (w == 0 && e < n) {
