@@ -199,6 +199,16 @@ __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
     double fit = 0.0;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int64_t i0 = (tile / tiles_n) * BT, j0 = (tile % tiles_n) * BT;
+        // this thread's 16 elements of V, requested now and used after the
+        // products: the loads are in flight while the tile is computed
+        float vv[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t gi = i0 + ty + 16 * i, gj = j0 + tx + 16 * j;
+                vv[i][j] = (gi < a.m && gj < a.n) ? a.V[gi * a.ldv + gj] : 0.f;
+            }
         float acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -206,13 +216,22 @@ __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
             for (int j = 0; j < 4; ++j)
                 acc[i][j] = 0.f;
         for (int k0 = 0; k0 < a.r; k0 += KC) {
+            constexpr int PER = BT * KC / 256;
+            float wv[PER], hv[PER];
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {   // every load before the first store
+                const int idx = tid + q * 256, rr = idx / KC, kk = idx % KC;
+                const int64_t gi = i0 + rr, gj = j0 + rr;
+                const int gk = k0 + kk;
+                wv[q] = (gi < a.m && gk < a.r) ? a.W[gi * a.r + gk] : 0.f;
+                hv[q] = (gj < a.n && gk < a.r) ? a.Ht[gj * a.r + gk] : 0.f;
+            }
             __syncthreads();
-            for (int idx = tid; idx < BT * KC; idx += 256) {
-                int rr = idx / KC, kk = idx - rr * KC;
-                int64_t gi = i0 + rr, gj = j0 + rr;
-                int gk = k0 + kk;
-                Ws[kk][rr] = (gi < a.m && gk < a.r) ? a.W[gi * a.r + gk] : 0.f;
-                Hs[kk][rr] = (gj < a.n && gk < a.r) ? a.Ht[gj * a.r + gk] : 0.f;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int idx = tid + q * 256, rr = idx / KC, kk = idx % KC;
+                Ws[kk][rr] = wv[q];
+                Hs[kk][rr] = hv[q];
             }
             __syncthreads();
 #pragma unroll 4
@@ -241,7 +260,7 @@ __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
             for (int j = 0; j < 4; ++j) {
                 int64_t gj = j0 + tx + 16 * j;
                 if (gj < a.n) {
-                    float e = a.V[gi * a.ldv + gj] - acc[i][j];
+                    float e = vv[i][j] - acc[i][j];
                     f32 = fmaf(e, e, f32);
                 }
             }
@@ -333,8 +352,25 @@ __global__ void __launch_bounds__(kRedThreads) k_sumsq(const T *__restrict__ x, 
     double s = 0.0;
     float g = 0.f;
     int cnt = 0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // four loads in flight per trip, squared and summed in element order
+    for (; e + 3 * st < n; e += 4 * st) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            v[u] = as_f<T>(x[e + u * st]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            g = fmaf(v[u], v[u], g);
+            if (++cnt == 16) {
+                s += (double)g;
+                g = 0.f;
+                cnt = 0;
+            }
+        }
+    }
+    for (; e < n; e += st) {
         float v = as_f<T>(x[e]);
         g = fmaf(v, v, g);
         if (++cnt == 16) {
