@@ -641,6 +641,8 @@ struct Loop {
     int r;
     unsigned *ticket;   // last-CTA counter of the factor preparation
     float *Pg;          // Gram partial slices
+    int Pg_slices;      // their capacity
+    bool fuse_prep;     // the NQP kernel's epilogue writes the Gram partials
     int gS_w, gS_h;     // gram splits for W (m rows) and Ht (n rows)
     float *Gw, *Gh;     // Grams without beta
     float *Qt, *d;
@@ -656,8 +658,7 @@ struct Loop {
 // The factor X just updated feeds the next half-step `next`: its Gram G,
 // next.Q = G + beta I, the rescaled Qt, d (Alg. 3) and the packed operand of
 // next's tensor-core cross term, in one launch.
-nmf_status enqueue_prep(nmf_handle h, Loop &L, const float *X, int64_t rows, float *G,
-                        HalfStep &next)
+PrepArgs prep_args(Loop &L, const float *X, int64_t rows, float *G, HalfStep &next)
 {
     PrepArgs a{};
     a.X = X;
@@ -676,13 +677,23 @@ nmf_status enqueue_prep(nmf_handle h, Loop &L, const float *X, int64_t rows, flo
         a.npad = tc_npad(L.r);
         a.kp = tc_kpad(rows, next.tc_mode);
     }
-    CK(launch_factor_prep(a, h->stream));
+    return a;
+}
+
+nmf_status enqueue_prep(nmf_handle h, Loop &L, const float *X, int64_t rows, float *G,
+                        HalfStep &next)
+{
+    CK(launch_factor_prep(prep_args(L, X, rows, G, next), h->stream));
     return NMF_OK;
 }
 
 // One half-step once Qt, d and the packed factor are in place: the cross
-// term C = V X_other, then every row's NQP (Alg. 3).
-nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s)
+// term C = V X_other, then every row's NQP (Alg. 3), then the preparation
+// of the solved factor for the half-step `next` (Gram G, Q, Qt, d, packing):
+// with fuse_prep the NQP kernel's epilogue writes the Gram partials and the
+// packed rows and one finishing launch follows; otherwise both launches of
+// the preparation follow.
+nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, float *G, HalfStep &next)
 {
     cudaStream_t st = h->stream;
     // cross term C = V X_other
@@ -720,9 +731,24 @@ nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s)
         a.maxstop_dev = s.ms_thr;
         a.s_final_max = s.ms_out;
     }
+    const PrepArgs pa = prep_args(L, s.X, s.rows, G, next);
+    int S = 0;
+    if (L.fuse_prep) {
+        a.gram_P = pa.P;
+        a.gram_smax = L.Pg_slices;
+        a.pack_mode = pa.pack_mode;
+        a.pack = pa.pack;
+        a.npad = pa.npad;
+        a.kp = pa.kp;
+        a.grid_out = &S;
+    }
     CK(launch_nnls(a, st));
     if (L.nn.maxstop_mode == 1)
         CK(cudaMemcpyAsync(s.ms_thr, s.ms_out, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
+    if (L.fuse_prep)
+        CK(launch_prep_finish(pa, S, st));
+    else
+        CK(launch_factor_prep(pa, st));
     return NMF_OK;
 }
 
@@ -733,17 +759,13 @@ nmf_status enqueue_iteration(nmf_handle h, Loop &L, const nmf_solve_opts &o)
 {
     (void)o;
     nmf_status s;
-    // W-update (E-step): C_W = V Ht against Q_W = Ht^T Ht + b_w I, ready
-    if ((s = enqueue_half(h, L, L.hw)))
+    // W-update (E-step): C_W = V Ht against Q_W = Ht^T Ht + b_w I, ready;
+    // then G_W = W^T W -> Q_H, Qt, d and packed W for the H-update
+    if ((s = enqueue_half(h, L, L.hw, L.Gw, L.hh)))
         return s;
-    // G_W = W^T W -> Q_H, Qt, d and packed W for the H-update
-    if ((s = enqueue_prep(h, L, L.hw.X, L.hw.rows, L.Gw, L.hh)))
-        return s;
-    // H-update (M-step)
-    if ((s = enqueue_half(h, L, L.hh)))
-        return s;
-    // G_H = Ht^T Ht -> Q_W, Qt, d and packed Ht for the next W-update
-    if ((s = enqueue_prep(h, L, L.hh.X, L.hh.rows, L.Gh, L.hw)))
+    // H-update (M-step); then G_H = Ht^T Ht -> Q_W, Qt, d and packed Ht for
+    // the next W-update
+    if ((s = enqueue_half(h, L, L.hh, L.Gh, L.hw)))
         return s;
     return NMF_OK;
 }
@@ -969,6 +991,15 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     {
         const int ps = prep_slices(m > n ? m : n);
         gS = ps > gS ? ps : gS;
+    }
+    // the NQP kernel prepares the factor it solved when its layout carries
+    // the epilogue (RP <= 64): one Gram partial per CTA
+    {
+        int lg = 0, lj = 0;
+        L.fuse_prep = nnls_layout(r, o.nnls.lanes, &lg, &lj) && lg * lj <= 64;
+        if (L.fuse_prep)
+            gS = gS > kPrepMaxSlices ? gS : kPrepMaxSlices;
+        L.Pg_slices = kPrepMaxSlices;
     }
     int sw = 1, sh = 1;
     SpmmPlan pw{}, ph{};

@@ -33,7 +33,7 @@
 // up its neighbours.  Idle groups ride along with zero steps, which leave
 // their state unchanged.
 #pragma once
-#include "nmf_internal.cuh"
+#include "k_prep.cuh"
 
 namespace nmfi {
 namespace nnls_detail {
@@ -268,11 +268,25 @@ __device__ __forceinline__ float proj_part(const float (&y)[J], const float (&g)
     return s;
 }
 
+// the epilogue that prepares the solved factor (Gram partial, packing) is
+// built for RP <= 64, where its accumulators fit the register budget
+template <int G, int J>
+constexpr bool has_prep_epilogue() { return Map<G, J>::RP <= 64; }
+
+template <int G, int J>
+constexpr int stage_floats()
+{
+    return has_prep_epilogue<G, J>()
+               ? prep_detail::kRowsBlock * (prep_detail::stage_cols(Map<G, J>::RP) + 1)
+               : 0;
+}
+
 template <int G, int J>
 constexpr size_t smem_bytes()
 {
     using M = Map<G, J>;
-    return sizeof(float) * ((size_t)M::RP * M::RP + M::RP + 2 * (size_t)kWarps * (32 / G) * M::VB);
+    return sizeof(float) * ((size_t)M::RP * M::RP + M::RP + 2 * (size_t)kWarps * (32 / G) * M::VB +
+                            stage_floats<G, J>());
 }
 
 // CTAs per SM the register budget is sized for
@@ -625,6 +639,26 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<J>()) k_nnls(const NnlsA
         }
         flush_warp_counters(a, c);
     }
+    // epilogue: this CTA's rows of the solved factor into Gram partial
+    // `blockIdx.x` and the packed operand of the next cross term (they are
+    // in memory: written by this CTA before the barrier above)
+    if constexpr (has_prep_epilogue<G, J>()) {
+        if (a.gram_P) {
+            constexpr int NBE = prep_detail::stage_cols(RP);
+            float(*Xs)[NBE + 1] = reinterpret_cast<float(*)[NBE + 1]>(
+                smem + RP * RP + RP + pool_floats<G, J>());
+            PrepArgs pa{};
+            pa.X = a.X;
+            pa.rows = a.rows;
+            pa.r = a.r;
+            pa.P = a.gram_P;
+            pa.pack_mode = a.pack_mode;
+            pa.pack = a.pack;
+            pa.npad = a.npad;
+            pa.kp = a.kp;
+            prep_detail::gram_pack_rows<NBE>(pa, Xs, lo, hi, blockIdx.x);
+        }
+    }
 }
 
 template <int G, int J>
@@ -697,7 +731,14 @@ cudaError_t launch(const NnlsArgs &a, cudaStream_t s)
     cudaError_t e = prepare<G, J>();
     if (e != cudaSuccess)
         return e;
-    const int grid = nnls_grid(a.rows, 32 / G, Cfg<G, J>::sms, Cfg<G, J>::blocks_per_sm);
+    int grid = nnls_grid(a.rows, 32 / G, Cfg<G, J>::sms, Cfg<G, J>::blocks_per_sm);
+    if (a.gram_P) {
+        if (!has_prep_epilogue<G, J>() || a.gram_smax < 1)
+            return cudaErrorInvalidValue;
+        grid = grid < a.gram_smax ? grid : a.gram_smax;
+    }
+    if (a.grid_out)
+        *a.grid_out = grid;
     if (grid < 1)
         return cudaSuccess;
     // an ordinary launch: started early beside the tensor-core kernel's tail

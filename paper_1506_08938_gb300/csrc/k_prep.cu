@@ -13,100 +13,22 @@
 //      (ticket counter) rescales and clears the counter.
 // Both kernels issue their global loads in batches before using them: a
 // load whose value is stored or added right away holds the next load back.
-#include "nmf_internal.cuh"
+#include "k_prep.cuh"
 
 namespace nmfi {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kRowsBlock = 32;     // rows staged in shared memory at a time
-constexpr int kMaxSlices = 512;    // Gram partials at most
+using namespace prep_detail;
 constexpr int kSumWarps = 16;      // warps of a reduction CTA
-
-// nearest TF32 value (10-bit mantissa)
-__device__ __forceinline__ float rn_tf32(float v)
-{
-    return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xffffe000u);
-}
 
 template <int NB>
 __global__ void __launch_bounds__(kThreads) k_factor_prep(const PrepArgs a)
 {
-    constexpr int T = NB / 16;
     __shared__ float Xs[kRowsBlock][NB + 1];
     pdl_trigger();   // the finishing kernel may launch; it waits for these partials
-    const int r = a.r, tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
     const int64_t k0 = (int64_t)blockIdx.x * a.chunk;
     const int64_t k1 = k0 + a.chunk < a.rows ? k0 + a.chunk : a.rows;
-    float acc[T][T];
-#pragma unroll
-    for (int i = 0; i < T; ++i)
-#pragma unroll
-        for (int j = 0; j < T; ++j)
-            acc[i][j] = 0.f;
-
-    for (int64_t kb = k0; kb < k1; kb += kRowsBlock) {
-        constexpr int PER = kRowsBlock * NB / kThreads;
-        float v[PER];
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int idx = tid + q * kThreads, kk = idx / NB, c = idx % NB;
-            const int64_t gk = kb + kk;
-            v[q] = (c < r && gk < k1) ? a.X[gk * r + c] : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int idx = tid + q * kThreads;
-            Xs[idx / NB][idx % NB] = v[q];
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < kRowsBlock; ++kk) {
-            float xa[T], xb[T];
-#pragma unroll
-            for (int i = 0; i < T; ++i)
-                xa[i] = Xs[kk][ti + 16 * i];
-#pragma unroll
-            for (int j = 0; j < T; ++j)
-                xb[j] = Xs[kk][tj + 16 * j];
-#pragma unroll
-            for (int i = 0; i < T; ++i)
-#pragma unroll
-                for (int j = 0; j < T; ++j)
-                    acc[i][j] = fmaf(xa[i], xb[j], acc[i][j]);
-        }
-        // packed operand: row n of the pack holds column n of X along k
-        if (a.pack_mode >= 0) {
-            for (int idx = tid; idx < a.npad * kRowsBlock; idx += kThreads) {
-                const int n = idx / kRowsBlock, kk = idx - n * kRowsBlock;
-                const int64_t gk = kb + kk;
-                if (gk >= k1)
-                    continue;
-                const float v = Xs[kk][n];   // zero for n >= r
-                const int64_t o = (int64_t)n * a.kp + gk;
-                if (a.pack_mode == TC_BF16) {
-                    reinterpret_cast<__nv_bfloat16 *>(a.pack)[o] = __float2bfloat16_rn(v);
-                } else if (a.pack_mode == TC_TF32X3) {
-                    const float hi = rn_tf32(v);
-                    reinterpret_cast<float *>(a.pack)[o] = hi;
-                    reinterpret_cast<float *>(a.pack)[(int64_t)a.npad * a.kp + o] =
-                        rn_tf32(v - hi);
-                } else {
-                    reinterpret_cast<float *>(a.pack)[o] = v;
-                }
-            }
-        }
-        __syncthreads();
-    }
-    float *Ps = a.P + (int64_t)blockIdx.x * r * r;
-#pragma unroll
-    for (int i = 0; i < T; ++i)
-#pragma unroll
-        for (int j = 0; j < T; ++j) {
-            const int ii = ti + 16 * i, jj = tj + 16 * j;
-            if (ii < r && jj < r)
-                Ps[ii * r + jj] = acc[i][j];
-        }
+    gram_pack_rows<NB>(a, Xs, k0, k1, blockIdx.x);
 }
 
 constexpr int kPerWarp = (kMaxSlices + kSumWarps - 1) / kSumWarps;   // slices per warp at most
@@ -231,6 +153,17 @@ cudaError_t launch_factor_prep(const PrepArgs &a0, cudaStream_t s)
         return e;
     const int n = a.r * a.r;
     e = pdl_launch(k_prep_finish, dim3((n + 31) / 32), dim3(kSumWarps * 32), 0, s, a, S);
+    count_launch();
+    return e;
+}
+
+cudaError_t launch_prep_finish(const PrepArgs &a, int S, cudaStream_t s)
+{
+    ProfScope prof_(KC_GRAM, s);
+    if (a.rows <= 0 || a.r < 1 || a.r > kMaxRank || !a.G || S < 1 || S > kMaxSlices)
+        return cudaErrorInvalidValue;
+    const int n = a.r * a.r;
+    cudaError_t e = pdl_launch(k_prep_finish, dim3((n + 31) / 32), dim3(kSumWarps * 32), 0, s, a, S);
     count_launch();
     return e;
 }

@@ -85,6 +85,17 @@ struct NnlsArgs {
     unsigned *s_final_max;  // optional: atomicMax of final ||f||^2 bits
     unsigned *status;       // optional device status word
     int lanes;              // lanes per row (0: chosen from r)
+    // optional epilogue (standalone kernel only): each CTA writes the Gram
+    // partial of its rows of the solved X into slice blockIdx of gram_P (r x r)
+    // and, if pack_mode >= 0, their columns of the packed operand; the grid
+    // is then at most gram_smax CTAs and its size is returned in *grid_out
+    float *gram_P;
+    int gram_smax;
+    int pack_mode;
+    void *pack;
+    int npad;
+    int64_t kp;
+    int *grid_out;          // host
 };
 cudaError_t launch_nnls(const NnlsArgs &a, cudaStream_t s);
 cudaError_t prepare_nnls(int r, int lanes);
@@ -109,7 +120,11 @@ struct PrepArgs {
     int64_t kp;
     int64_t chunk;          // rows per CTA (set by the launcher)
 };
+constexpr int kPrepMaxSlices = 512;   // Gram partial slices the finishing kernel sums at most
 cudaError_t launch_factor_prep(const PrepArgs &a, cudaStream_t s);
+// the second launch alone, over S partial slices already in a.P (written by
+// the NQP kernel's epilogue)
+cudaError_t launch_prep_finish(const PrepArgs &a, int S, cudaStream_t s);
 int prep_slices(int64_t rows);
 
 // ---- Gram / cross term (SIMT FP32) ----------------------------------------
