@@ -185,12 +185,15 @@ __global__ void __launch_bounds__(256) k_kkt(const float *__restrict__ Q,
 // summed in FP32 over the thread's 16 elements of a 64 x 64 tile, the tile
 // sums in FP64.  Avoids the cancellation of the trace identity.  Persistent
 // CTAs walk the tiles; FP64 arithmetic (a small fraction of FP32 throughput
-// on this part) is kept to one add per thread per tile.
+// on this part) is kept to one add per thread per tile.  A thread owns a
+// 4 x 4 block (rows ty*4.., columns tx*4..), read from the staged factors as
+// one 16-byte load each per k (rows padded to 68 floats: 16-byte aligned,
+// at most 4-way conflicts while staging).
 __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
 {
-    constexpr int BT = 64, KC = 32;
-    __shared__ float Ws[KC][BT + 1];
-    __shared__ float Hs[KC][BT + 1];
+    constexpr int BT = 64, KC = 32, LD = BT + 4;
+    __shared__ __align__(16) float Ws[KC][LD];
+    __shared__ __align__(16) float Hs[KC][LD];
     __shared__ double sh[32];
     __shared__ bool last;
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int64_t gi = i0 + ty + 16 * i, gj = j0 + tx + 16 * j;
+                const int64_t gi = i0 + ty * 4 + i, gj = j0 + tx * 4 + j;
                 vv[i][j] = (gi < a.m && gj < a.n) ? a.V[gi * a.ldv + gj] : 0.f;
             }
         float acc[4][4];
@@ -234,15 +237,13 @@ __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
                 Hs[kk][rr] = hv[q];
             }
             __syncthreads();
+            const int kc = a.r - k0 < KC ? a.r - k0 : KC;   // columns of this chunk
 #pragma unroll 4
-            for (int kk = 0; kk < KC; ++kk) {
-                float w[4], hh[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    w[i] = Ws[kk][ty + 16 * i];
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    hh[j] = Hs[kk][tx + 16 * j];
+            for (int kk = 0; kk < kc; ++kk) {
+                const float4 w4 = *reinterpret_cast<const float4 *>(&Ws[kk][ty * 4]);
+                const float4 h4 = *reinterpret_cast<const float4 *>(&Hs[kk][tx * 4]);
+                const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+                const float hh[4] = {h4.x, h4.y, h4.z, h4.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -253,12 +254,12 @@ __global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
         float f32 = 0.f;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            int64_t gi = i0 + ty + 16 * i;
+            int64_t gi = i0 + ty * 4 + i;
             if (gi >= a.m)
                 continue;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                int64_t gj = j0 + tx + 16 * j;
+                int64_t gj = j0 + tx * 4 + j;
                 if (gj < a.n) {
                     float e = vv[i][j] - acc[i][j];
                     f32 = fmaf(e, e, f32);
