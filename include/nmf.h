@@ -218,7 +218,8 @@ nmf_status nmf_objective_direct(nmf_handle h, const nmf_dense *V, const float *W
                                 double *J_dev);
 
 /* KKT residuals of Eq. 2 for one factor, in FP64: with
- * grad_i = Q X_i - C_i + alpha (Q r x r including the L2 term),
+ * grad_i = Q X_i - C_i + alpha (Q r x r including the L2 term; symmetric, as
+ * every Gram is - it is read by columns),
  * out_dev[0] = max |min(X_ij, grad_ij)|, out_dev[1] = max |X_ij grad_ij|. */
 nmf_status nmf_kkt(nmf_handle h, const float *Q, const float *C, int64_t rows, int r,
                    float alpha, const float *X, double *out_dev);

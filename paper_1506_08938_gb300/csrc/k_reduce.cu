@@ -145,7 +145,9 @@ __global__ void __launch_bounds__(kRedThreads) k_objective(const ObjArgs a)
     }
 }
 
-// KKT residuals of one factor, FP64.  One warp per row; Q and the row in smem.
+// KKT residuals of one factor, FP64.  One warp per row, the row in smem;
+// lane j forms (Q x)_j reading Q by columns (Q symmetric), so for each k the
+// lanes read one contiguous run of Q instead of 32 separate rows.
 __global__ void __launch_bounds__(256) k_kkt(const float *__restrict__ Q,
                                              const float *__restrict__ C, int64_t rows, int r,
                                              float alpha, const float *__restrict__ X,
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(256) k_kkt(const float *__restrict__ Q,
         for (int j = lane; j < r; j += 32) {
             double gj = (double)alpha - (double)C[row * r + j];
             for (int k = 0; k < r; ++k)
-                gj += (double)__ldg(Q + j * r + k) * (double)sx[w][k];
+                gj += (double)__ldg(Q + k * r + j) * (double)sx[w][k];
             const double x = (double)sx[w][j];
             const double a1 = fabs(x < gj ? x : gj), a2 = fabs(x * gj);
             m1 = a1 > m1 ? a1 : m1;

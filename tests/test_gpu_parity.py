@@ -378,6 +378,29 @@ def test_one_iteration_from_oracle_state(h, r, t0):
     assert abs(hist[0] - ho[1]) / ho[1] < j_bound(inst, Wo, Ho, tw, th)
 
 
+@pytest.mark.parametrize("r", [64, 80])
+def test_converged_iteration_both_preparations(h, r):
+    """One outer iteration with every NQP solved to its unique minimiser,
+    from the seeded start: at r = 64 the NQP kernel's epilogue prepares the
+    solved factor (Gram partials, packed operand) for the next half-step, at
+    r = 80 (RP = 128) the separate preparation kernels do; both against the
+    oracle's converged iteration within the derived FP32 bounds."""
+    inst = f32_inst(WL.tiny(seed=1, r=r, m=300, n=260))
+    inst.beta_w = inst.beta_h = 0.1
+    Wo, Ho, _, _ = O.nmf_solve(inst.W0, inst.Ht0, 1, V=inst.V, beta_w=0.1, beta_h=0.1,
+                               opts=O.nqp_opts(max_inner=5000, eps=0.0, abs_tol=1e-24))
+    W, Ht, hist, rep = run_solve(h, inst, 1, 400, eps=1e-12, objective="direct")
+    tw, _ = step_bounds(Wo, inst.Ht0, r, 0.1, 0.1)
+    assert rel_err(to_np(W), Wo) < tw
+    # the H-update against the oracle's unique minimisers for the GPU's own W
+    # (the W error carried through an ill-conditioned Q_H would make a loose bound)
+    Wg = to_np(W).astype(np.float64)
+    Qh = O.gram(Wg, 0.1)
+    Hs, *_ = O.nnls_update(Qh, O.cross_dense(inst.V.T, Wg), 0.0, inst.Ht0,
+                           O.nqp_opts(max_inner=5000, eps=0.0, abs_tol=1e-24))
+    assert rel_err(to_np(Ht), Hs) < nnls_tol(Qh, r)
+
+
 def horizon(inst, T, K, **kw):
     """1/(1 - rho), rho = ||W_T - W_{T-1}|| / ||W_{T-1} - W_{T-2}|| on the
     oracle's own trajectory (a contracting iteration sums per-step errors over
