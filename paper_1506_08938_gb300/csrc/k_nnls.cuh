@@ -31,7 +31,15 @@
 // meets the stop rule writes it out and takes the next row of the warp's
 // share in the next round, so a row that needs many iterations does not hold
 // up its neighbours.  Idle groups ride along with zero steps, which leave
-// their state unchanged.
+// their state unchanged.  The standalone kernel gives each CTA a balanced
+// contiguous range of rows and each warp runs of 32/G consecutive rows of
+// it; the line search's matrix-vector products share each Qt load among the
+// groups of a warp (matvec_coop).
+//
+// Epilogue (optional, RP <= 64): each CTA turns its rows of the solved
+// factor into one Gram partial and their columns of the packed tensor-core
+// operand for the next half-step (k_prep.cuh), so the next half-step's
+// preparation needs only the finishing launch.
 #pragma once
 #include "k_prep.cuh"
 
