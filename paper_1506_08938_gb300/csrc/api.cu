@@ -983,6 +983,13 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     if (m <= 0 || n <= 0)
         return NMF_E_SHAPE;
     CK(cudaSetDevice(h->device));
+    // Wide factors of large problems: at r > 64 with tens of thousands of
+    // rows in both half-steps, 8 lanes per row (16 coordinates each) beat the
+    // default 16 (8 each) by ~20% (fewer instructions per coordinate step
+    // when many rounds of rows keep the SMs issue-bound; measured at r = 100
+    // on 50000 and 100000 rows).  The layout is fixed for the whole solve.
+    if (L.nn.lanes == 0 && r > 64 && (m < n ? m : n) >= 32768)
+        L.nn.lanes = 8;
 
     // ---- workspace layout
     L.gS_w = gram_splits(m);
@@ -996,7 +1003,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     // the epilogue (RP <= 64): one Gram partial per CTA
     {
         int lg = 0, lj = 0;
-        L.fuse_prep = nnls_layout(r, o.nnls.lanes, &lg, &lj) && lg * lj <= 64;
+        L.fuse_prep = nnls_layout(r, L.nn.lanes, &lg, &lj) && lg * lj <= 64;
         if (L.fuse_prep)
             gS = gS > kPrepMaxSlices ? gS : kPrepMaxSlices;
         L.Pg_slices = kPrepMaxSlices;
