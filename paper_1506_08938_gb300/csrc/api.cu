@@ -138,6 +138,8 @@ struct nmf_ctx {
     unsigned *smax = nullptr;    // 2 words (maxStop bits per factor)
     cudaStream_t cap = nullptr;  // private stream for graph capture (the
                                  // legacy default stream cannot be captured)
+    cudaStream_t side = nullptr; // second stream of the solve (work beside the cross term)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     char *stage = nullptr;       // device copies of host-resident solve inputs
     size_t stage_cap = 0;
 };
@@ -331,6 +333,14 @@ NMF_API nmf_status nmf_destroy(nmf_handle h)
         cudaFree(h->ws);
     if (h->cap)
         cudaStreamDestroy(h->cap);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    if (h->ev_fork)
+        cudaEventDestroy(h->ev_fork);
+    if (h->ev_join)
+        cudaEventDestroy(h->ev_join);
     if (h->stage)
         cudaFree(h->stage);
     cudaFree(h->status);   // first allocation of the aux block
@@ -643,6 +653,8 @@ struct Loop {
     float *Pg;          // Gram partial slices
     int Pg_slices;      // their capacity
     bool fuse_prep;     // the NQP kernel's epilogue writes the Gram partials
+    bool overlap_prep;  // ... and their finishing launch runs beside the cross term
+    int S_w, S_h;       // with overlap_prep: partials of W (m rows) and Ht (n rows)
     int gS_w, gS_h;     // gram splits for W (m rows) and Ht (n rows)
     float *Gw, *Gh;     // Grams without beta
     float *Qt, *d;
@@ -680,22 +692,39 @@ PrepArgs prep_args(Loop &L, const float *X, int64_t rows, float *G, HalfStep &ne
     return a;
 }
 
-nmf_status enqueue_prep(nmf_handle h, Loop &L, const float *X, int64_t rows, float *G,
-                        HalfStep &next)
+// The finishing launch of the half-step `s`'s own preparation: G_other,
+// s.Q, Qt, d from the Gram partials of its other factor (the packed operand
+// is already in place, its padding zeroed by the epilogue that packed it).
+PrepArgs finish_args(Loop &L, HalfStep &s, float *G_other)
 {
-    CK(launch_factor_prep(prep_args(L, X, rows, G, next), h->stream));
-    return NMF_OK;
+    PrepArgs a = prep_args(L, s.Xo, s.Ko, G_other, s);
+    a.pack_mode = -1;
+    return a;
 }
 
-// One half-step once Qt, d and the packed factor are in place: the cross
-// term C = V X_other, then every row's NQP (Alg. 3), then the preparation
-// of the solved factor for the half-step `next` (Gram G, Q, Qt, d, packing):
-// with fuse_prep the NQP kernel's epilogue writes the Gram partials and the
-// packed rows and one finishing launch follows; otherwise both launches of
-// the preparation follow.
-nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, float *G, HalfStep &next)
+constexpr int kSideCtas = 8;   // SMs the cross term leaves to the finishing launch
+
+// One half-step: the cross term C = V X_other, every row's NQP (Alg. 3),
+// and the preparation of the solved factor for the half-step `next` (Gram G,
+// Q, Qt, d, packing).  With fuse_prep the NQP kernel's epilogue writes the
+// Gram partials and the packed rows; the finishing launch then either
+// follows the NQP launch, or (overlap_prep) runs at the start of `next` on
+// the side stream on kSideCtas SMs beside `next`'s cross term - which needs
+// only the packed operand and is planned for the other SMs - and joins
+// before `next`'s NQP launch.  Without fuse_prep both launches of the
+// preparation follow the NQP launch.
+nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, float *G, HalfStep &next,
+                        float *G_other)
 {
     cudaStream_t st = h->stream;
+    const bool is_w = &s == &L.hw;
+    if (L.overlap_prep) {
+        CK(cudaEventRecord(h->ev_fork, st));
+        CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        CK(launch_prep_finish_narrow(finish_args(L, s, G_other), is_w ? L.S_h : L.S_w, kSideCtas,
+                                     h->side));
+        CK(cudaEventRecord(h->ev_join, h->side));
+    }
     // cross term C = V X_other
     if (s.sparse) {
         CK(launch_spmm_csr(s.csr->rowptr, s.csr->colidx, s.csr->vals, s.csr->dt, s.csr->rows,
@@ -706,6 +735,8 @@ nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, float *G, HalfStep &
     } else {
         CK(launch_cross_dense_f32(s.A, s.rows, s.K, s.lda, s.Xo, L.r, s.Cs, s.nsplit, st));
     }
+    if (L.overlap_prep)
+        CK(cudaStreamWaitEvent(st, h->ev_join, 0));
     NnlsArgs a{};
     a.Qt = L.Qt;
     a.d = L.d;
@@ -743,8 +774,12 @@ nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, float *G, HalfStep &
         a.grid_out = &S;
     }
     CK(launch_nnls(a, st));
+    if (L.overlap_prep && S != (is_w ? L.S_w : L.S_h))
+        return NMF_E_ARG;   // the partial count the next finishing launch expects
     if (L.nn.maxstop_mode == 1)
         CK(cudaMemcpyAsync(s.ms_thr, s.ms_out, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
+    if (L.overlap_prep)
+        return NMF_OK;
     if (L.fuse_prep)
         CK(launch_prep_finish(pa, S, st));
     else
@@ -761,11 +796,11 @@ nmf_status enqueue_iteration(nmf_handle h, Loop &L, const nmf_solve_opts &o)
     nmf_status s;
     // W-update (E-step): C_W = V Ht against Q_W = Ht^T Ht + b_w I, ready;
     // then G_W = W^T W -> Q_H, Qt, d and packed W for the H-update
-    if ((s = enqueue_half(h, L, L.hw, L.Gw, L.hh)))
+    if ((s = enqueue_half(h, L, L.hw, L.Gw, L.hh, L.Gh)))
         return s;
     // H-update (M-step); then G_H = Ht^T Ht -> Q_W, Qt, d and packed Ht for
     // the next W-update
-    if ((s = enqueue_half(h, L, L.hh, L.Gh, L.hw)))
+    if ((s = enqueue_half(h, L, L.hh, L.Gh, L.hw, L.Gw)))
         return s;
     return NMF_OK;
 }
@@ -792,7 +827,11 @@ nmf_status enqueue_objective(nmf_handle h, Loop &L, const nmf_solve_opts &o, dou
         CK(launch_objective_direct(b, h->stream));
         return NMF_OK;
     }
-    // J(W, H) by the FP64 trace identity
+    // J(W, H) by the FP64 trace identity.  With overlap_prep G_H = Ht^T Ht is
+    // finished at the start of the next W-update; finish it now for the
+    // objective (the next W-update's finishing launch writes the same values)
+    if (L.overlap_prep)
+        CK(launch_prep_finish(finish_args(L, L.hw, L.Gh), L.S_h, h->stream));
     ObjArgs a{};
     a.vv = L.vv;
     a.W = L.hw.X;
@@ -1034,9 +1073,17 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
             else if (o.prec == NMF_PREC_TF32)
                 return NMF_E_NOTIMPL;
         }
+        // the finishing launch of the preparation runs beside the cross term
+        // when the NQP epilogue writes the partials and the cross term is the
+        // tensor-core one: the cross term's stream-K plan leaves it SMs
+        L.overlap_prep = L.fuse_prep && mode >= 0;
         if (mode >= 0) {
-            L.hw.plan = tc_plan(m, n, r, mode);
-            L.hh.plan = tc_plan(n, m, r, mode);
+            int sms = 0, dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int cap = L.overlap_prep && sms > 2 * kSideCtas ? sms - kSideCtas : 0;
+            L.hw.plan = tc_plan(m, n, r, mode, cap);
+            L.hh.plan = tc_plan(n, m, r, mode, cap);
             sw = L.hw.plan.nslices;
             sh = L.hh.plan.nslices;
         }
@@ -1177,14 +1224,39 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     CK(cudaMemcpyAsync(&L.vv, vv_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
 
+    if (L.overlap_prep) {
+        // the NQP launches' grids are the partial counts of the finishing launches
+        NnlsArgs q{};
+        q.r = r;
+        q.lanes = L.nn.lanes;
+        q.gram_P = L.Pg;
+        q.gram_smax = L.Pg_slices;
+        q.rows = m;
+        L.S_w = nnls_grid_query(q);
+        q.rows = n;
+        L.S_h = nnls_grid_query(q);
+        if (L.S_w < 1 || L.S_h < 1)
+            return NMF_E_CUDA;
+        if (!h->side)
+            CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        if (!h->ev_fork)
+            CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        if (!h->ev_join)
+            CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, s));
-    // G_H = Ht^T Ht, Q_W, Qt, d and packed Ht for the first W-update
-    st = enqueue_prep(h, L, Ht, n, L.Gh, hw);
-    if (st)
-        return st;
+    // G_H = Ht^T Ht, Q_W, Qt, d and packed Ht for the first W-update; with
+    // overlap_prep its partials are split as the H-update's NQP launch splits
+    // them, since the first W-update's finishing launch sums them again
+    {
+        PrepArgs pa = prep_args(L, Ht, n, L.Gh, hw);
+        if (L.overlap_prep)
+            pa.slices = L.S_h;
+        CK(launch_factor_prep(pa, s));
+    }
 
     const bool gap_on = o.rel_gap_target > 0.0 && o.f_star > 0.0;
     const bool adaptive = o.check_every < 0;

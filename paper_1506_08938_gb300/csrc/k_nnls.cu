@@ -47,6 +47,17 @@ cudaError_t prepare_nnls(int r, int lanes)
     return nnls_go(a, r, lanes, true, nullptr);
 }
 
+int nnls_grid_query(const NnlsArgs &a0)
+{
+    NnlsArgs a = a0;
+    int g = 0;
+    a.grid_query = true;
+    a.grid_out = &g;
+    if (a.rows <= 0 || nnls_go(a, a.r, a.lanes, false, nullptr) != cudaSuccess)
+        return 0;
+    return g;
+}
+
 cudaError_t launch_nnls(const NnlsArgs &a, cudaStream_t s)
 {
     ProfScope prof_(KC_NNLS, s);

@@ -665,6 +665,9 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<J>()) k_nnls(const NnlsA
             pa.npad = a.npad;
             pa.kp = a.kp;
             prep_detail::gram_pack_rows<NBE>(pa, Xs, lo, hi, blockIdx.x);
+            // CTA 0 zeroes the pack's k padding (columns rows .. kp-1)
+            if (blockIdx.x == 0 && a.pack_mode >= 0)
+                prep_detail::zero_pack_padding(pa);
         }
     }
 }
@@ -747,7 +750,7 @@ cudaError_t launch(const NnlsArgs &a, cudaStream_t s)
     }
     if (a.grid_out)
         *a.grid_out = grid;
-    if (grid < 1)
+    if (grid < 1 || a.grid_query)
         return cudaSuccess;
     // an ordinary launch: started early beside the tensor-core kernel's tail
     // this latency-bound kernel measured slower, not faster

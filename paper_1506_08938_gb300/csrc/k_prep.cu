@@ -26,14 +26,21 @@ __global__ void __launch_bounds__(kThreads) k_factor_prep(const PrepArgs a)
 {
     __shared__ float Xs[kRowsBlock][NB + 1];
     pdl_trigger();   // the finishing kernel may launch; it waits for these partials
-    const int64_t k0 = (int64_t)blockIdx.x * a.chunk;
-    const int64_t k1 = k0 + a.chunk < a.rows ? k0 + a.chunk : a.rows;
+    int64_t k0, k1;
+    if (a.slices > 0) {   // the NQP kernel's balanced split
+        k0 = (int64_t)blockIdx.x * a.rows / gridDim.x;
+        k1 = (int64_t)(blockIdx.x + 1) * a.rows / gridDim.x;
+    } else {
+        k0 = (int64_t)blockIdx.x * a.chunk;
+        k1 = k0 + a.chunk < a.rows ? k0 + a.chunk : a.rows;
+    }
     gram_pack_rows<NB>(a, Xs, k0, k1, blockIdx.x);
 }
 
 constexpr int kPerWarp = (kMaxSlices + kSumWarps - 1) / kSumWarps;   // slices per warp at most
 
-// G[e] = sum_s P[s][e] for 32 consecutive e per CTA, then (last CTA) Q, Qt, d
+// G[e] = sum_s P[s][e] for groups of 32 consecutive e (group g on CTA
+// g mod gridDim.x), then (last CTA) Q, Qt, d
 __global__ void __launch_bounds__(kSumWarps * 32) k_prep_finish(const PrepArgs a, int S)
 {
     __shared__ float part[kSumWarps][33];
@@ -43,8 +50,8 @@ __global__ void __launch_bounds__(kSumWarps * 32) k_prep_finish(const PrepArgs a
     pdl_wait();   // the partials are the previous kernel's output
     const int r = a.r, n = r * r;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int e = blockIdx.x * 32 + lane;
-    {
+    for (int eg = blockIdx.x; eg * 32 < n; eg += gridDim.x) {
+        const int e = eg * 32 + lane;
         // this warp's slices w, w + kSumWarps, ... in order, every load
         // issued before the first add
         float v[kPerWarp];
@@ -58,14 +65,15 @@ __global__ void __launch_bounds__(kSumWarps * 32) k_prep_finish(const PrepArgs a
         for (int u = 0; u < kPerWarp; ++u)
             acc += v[u];
         part[w][lane] = acc;
-    }
-    __syncthreads();
-    if (w == 0 && e < n) {
-        float s = 0.f;
+        __syncthreads();
+        if (w == 0 && e < n) {
+            float s = 0.f;
 #pragma unroll
-        for (int q = 0; q < kSumWarps; ++q)
-            s += part[q][lane];
-        a.G[e] = s;
+            for (int q = 0; q < kSumWarps; ++q)
+                s += part[q][lane];
+            a.G[e] = s;
+        }
+        __syncthreads();   // part is rewritten by the next group
     }
     __threadfence();
     __syncthreads();
@@ -97,19 +105,8 @@ __global__ void __launch_bounds__(kSumWarps * 32) k_prep_finish(const PrepArgs a
         a.Qt[f] = v;
     }
     // zero columns K .. kp-1 of the pack (k padding of the last k block)
-    if (a.pack_mode >= 0) {
-        const int64_t padk = a.kp - a.rows;
-        for (int64_t idx = threadIdx.x; idx < (int64_t)a.npad * padk; idx += blockDim.x) {
-            const int64_t nn = idx / padk, o = nn * a.kp + a.rows + (idx - nn * padk);
-            if (a.pack_mode == TC_BF16) {
-                reinterpret_cast<__nv_bfloat16 *>(a.pack)[o] = __float2bfloat16_rn(0.f);
-            } else {
-                reinterpret_cast<float *>(a.pack)[o] = 0.f;
-                if (a.pack_mode == TC_TF32X3)
-                    reinterpret_cast<float *>(a.pack)[(int64_t)a.npad * a.kp + o] = 0.f;
-            }
-        }
-    }
+    if (a.pack_mode >= 0)
+        zero_pack_padding(a);
     if (threadIdx.x == 0)
         *a.ticket = 0u;   // ready for the next launch (graph replays included)
 }
@@ -138,7 +135,9 @@ cudaError_t launch_factor_prep(const PrepArgs &a0, cudaStream_t s)
     if (a.rows <= 0 || a.r < 1 || a.r > kMaxRank || !a.G)
         return cudaErrorInvalidValue;
     a.chunk = prep_chunk(a.rows);
-    const int S = prep_slices(a.rows);
+    const int S = a.slices > 0 ? a.slices : prep_slices(a.rows);
+    if (S > kMaxSlices)
+        return cudaErrorInvalidValue;
     // the partials kernel follows the latency-bound NQP kernel: an ordinary
     // launch; the finishing kernel may start while the partials drain
     if (a.r <= 32)
@@ -155,6 +154,17 @@ cudaError_t launch_factor_prep(const PrepArgs &a0, cudaStream_t s)
     e = pdl_launch(k_prep_finish, dim3((n + 31) / 32), dim3(kSumWarps * 32), 0, s, a, S);
     count_launch();
     return e;
+}
+
+cudaError_t launch_prep_finish_narrow(const PrepArgs &a, int S, int ctas, cudaStream_t s)
+{
+    ProfScope prof_(KC_GRAM, s);
+    if (a.rows <= 0 || a.r < 1 || a.r > kMaxRank || !a.G || S < 1 || S > kMaxSlices || ctas < 1)
+        return cudaErrorInvalidValue;
+    const int groups = (a.r * a.r + 31) / 32;
+    k_prep_finish<<<ctas < groups ? ctas : groups, kSumWarps * 32, 0, s>>>(a, S);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_prep_finish(const PrepArgs &a, int S, cudaStream_t s)

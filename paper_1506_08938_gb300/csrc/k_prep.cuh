@@ -100,6 +100,23 @@ __device__ __forceinline__ void gram_pack_rows(const PrepArgs &a, float (*Xs)[NB
         }
 }
 
+// columns rows .. kp-1 of the packed operand (the k padding of its last k
+// block) set to zero by the calling CTA
+__device__ __forceinline__ void zero_pack_padding(const PrepArgs &a)
+{
+    const int64_t padk = a.kp - a.rows;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)a.npad * padk; idx += blockDim.x) {
+        const int64_t nn = idx / padk, o = nn * a.kp + a.rows + (idx - nn * padk);
+        if (a.pack_mode == TC_BF16) {
+            reinterpret_cast<__nv_bfloat16 *>(a.pack)[o] = __float2bfloat16_rn(0.f);
+        } else {
+            reinterpret_cast<float *>(a.pack)[o] = 0.f;
+            if (a.pack_mode == TC_TF32X3)
+                reinterpret_cast<float *>(a.pack)[(int64_t)a.npad * a.kp + o] = 0.f;
+        }
+    }
+}
+
 // columns of the staging block for a factor of at most `cols` columns
 __host__ __device__ constexpr int stage_cols(int cols) { return cols <= 32 ? 32 : (cols <= 64 ? 64 : 128); }
 

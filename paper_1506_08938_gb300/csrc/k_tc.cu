@@ -908,7 +908,7 @@ bool tc_supported(int64_t lda, int mode, const void *A)
     return (lda % align) == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0 && encode_fn();
 }
 
-TcPlan tc_plan(int64_t M, int64_t K, int r, int mode)
+TcPlan tc_plan(int64_t M, int64_t K, int r, int mode, int max_grid)
 {
     TcPlan pl;
     const int kstep = mode == TC_BF16 ? 64 : 32;
@@ -916,6 +916,8 @@ TcPlan tc_plan(int64_t M, int64_t K, int r, int mode)
     pl.tiles = (int)((M + 127) / 128);
     pl.iters = (int64_t)pl.tiles * pl.kblocks;
     int g = sm_count();
+    if (max_grid > 0 && max_grid < g)
+        g = max_grid;
     if (pl.iters < g)
         g = (int)pl.iters;
     pl.grid = g < 1 ? 1 : g;

@@ -96,8 +96,10 @@ struct NnlsArgs {
     int npad;
     int64_t kp;
     int *grid_out;          // host
+    bool grid_query;        // host: only compute the grid into *grid_out
 };
 cudaError_t launch_nnls(const NnlsArgs &a, cudaStream_t s);
+int nnls_grid_query(const NnlsArgs &a);   // the grid launch_nnls would use (0 on error)
 cudaError_t prepare_nnls(int r, int lanes);
 bool nnls_layout(int r, int lanes, int *G, int *J);
 
@@ -119,12 +121,17 @@ struct PrepArgs {
     int npad;
     int64_t kp;
     int64_t chunk;          // rows per CTA (set by the launcher)
+    int slices;             // > 0: that many partial slices over balanced row ranges
+                            // (the NQP kernel's split); 0: 32-row chunks
 };
 constexpr int kPrepMaxSlices = 512;   // Gram partial slices the finishing kernel sums at most
 cudaError_t launch_factor_prep(const PrepArgs &a, cudaStream_t s);
 // the second launch alone, over S partial slices already in a.P (written by
 // the NQP kernel's epilogue)
 cudaError_t launch_prep_finish(const PrepArgs &a, int S, cudaStream_t s);
+// the same on `ctas` CTAs (each walks several 32-element groups), an ordinary
+// launch: for a side stream, beside the cross term
+cudaError_t launch_prep_finish_narrow(const PrepArgs &a, int S, int ctas, cudaStream_t s);
 int prep_slices(int64_t rows);
 
 // ---- Gram / cross term (SIMT FP32) ----------------------------------------
@@ -163,7 +170,8 @@ int tc_npad(int r);
 int64_t tc_kpad(int64_t K, int mode);
 size_t tc_pack_bytes(int64_t K, int r, int mode);
 bool tc_supported(int64_t lda, int mode, const void *A);
-TcPlan tc_plan(int64_t M, int64_t K, int r, int mode);
+// max_grid > 0 caps the CTAs (SMs left free for work beside the cross term)
+TcPlan tc_plan(int64_t M, int64_t K, int r, int mode, int max_grid = 0);
 // pack X (K x r row-major FP32) as the B operand of mode `mode`
 cudaError_t launch_tc_pack(const float *X, int64_t K, int r, int mode, void *pack, cudaStream_t s);
 cudaError_t launch_tc_cross(const void *A, int64_t M, int64_t K, int64_t lda, int r, int mode,
