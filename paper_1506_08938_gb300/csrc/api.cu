@@ -654,6 +654,8 @@ struct Loop {
     int Pg_slices;      // their capacity
     bool fuse_prep;     // the NQP kernel's epilogue writes the Gram partials
     bool overlap_prep;  // ... and their finishing launch runs beside the cross term
+    bool overlap_full;  // no epilogue: the whole preparation runs beside a cross
+                        // term that reads the other factor itself (CSR, CUDA cores)
     int S_w, S_h;       // with overlap_prep: partials of W (m rows) and Ht (n rows)
     int gS_w, gS_h;     // gram splits for W (m rows) and Ht (n rows)
     float *Gw, *Gh;     // Grams without beta
@@ -707,22 +709,28 @@ constexpr int kSideCtas = 8;   // SMs the cross term leaves to the finishing lau
 // One half-step: the cross term C = V X_other, every row's NQP (Alg. 3),
 // and the preparation of the solved factor for the half-step `next` (Gram G,
 // Q, Qt, d, packing).  With fuse_prep the NQP kernel's epilogue writes the
-// Gram partials and the packed rows; the finishing launch then either
-// follows the NQP launch, or (overlap_prep) runs at the start of `next` on
-// the side stream on kSideCtas SMs beside `next`'s cross term - which needs
-// only the packed operand and is planned for the other SMs - and joins
-// before `next`'s NQP launch.  Without fuse_prep both launches of the
-// preparation follow the NQP launch.
+// Gram partials and the packed rows, and the finishing launch (overlap_prep)
+// runs at the start of `next` on the side stream beside `next`'s cross term -
+// which needs only the packed operand (or the factor itself) and, on tensor
+// cores, is planned for the SMs the finishing launch's kSideCtas CTAs leave
+// - joining before `next`'s NQP launch.  Without the epilogue, a cross term
+// that reads the other factor itself (CSR, CUDA cores) runs beside the whole
+// preparation (overlap_full); the tensor-core cross term needs the packed
+// operand, so there both launches of the preparation follow the NQP launch.
 nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, float *G, HalfStep &next,
                         float *G_other)
 {
     cudaStream_t st = h->stream;
     const bool is_w = &s == &L.hw;
-    if (L.overlap_prep) {
+    const bool side = L.overlap_prep || L.overlap_full;
+    if (side) {
         CK(cudaEventRecord(h->ev_fork, st));
         CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-        CK(launch_prep_finish_narrow(finish_args(L, s, G_other), is_w ? L.S_h : L.S_w, kSideCtas,
-                                     h->side));
+        if (L.overlap_prep)
+            CK(launch_prep_finish_narrow(finish_args(L, s, G_other), is_w ? L.S_h : L.S_w,
+                                         kSideCtas, h->side));
+        else
+            CK(launch_factor_prep(prep_args(L, s.Xo, s.Ko, G_other, s), h->side));
         CK(cudaEventRecord(h->ev_join, h->side));
     }
     // cross term C = V X_other
@@ -735,7 +743,7 @@ nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, float *G, HalfStep &
     } else {
         CK(launch_cross_dense_f32(s.A, s.rows, s.K, s.lda, s.Xo, L.r, s.Cs, s.nsplit, st));
     }
-    if (L.overlap_prep)
+    if (side)
         CK(cudaStreamWaitEvent(st, h->ev_join, 0));
     NnlsArgs a{};
     a.Qt = L.Qt;
@@ -778,7 +786,7 @@ nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, float *G, HalfStep &
         return NMF_E_ARG;   // the partial count the next finishing launch expects
     if (L.nn.maxstop_mode == 1)
         CK(cudaMemcpyAsync(s.ms_thr, s.ms_out, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
-    if (L.overlap_prep)
+    if (side)
         return NMF_OK;
     if (L.fuse_prep)
         CK(launch_prep_finish(pa, S, st));
@@ -832,6 +840,8 @@ nmf_status enqueue_objective(nmf_handle h, Loop &L, const nmf_solve_opts &o, dou
     // objective (the next W-update's finishing launch writes the same values)
     if (L.overlap_prep)
         CK(launch_prep_finish(finish_args(L, L.hw, L.Gh), L.S_h, h->stream));
+    else if (L.overlap_full)
+        CK(launch_factor_prep(prep_args(L, L.hw.Xo, L.hw.Ko, L.Gh, L.hw), h->stream));
     ObjArgs a{};
     a.vv = L.vv;
     a.W = L.hw.X;
@@ -1073,21 +1083,24 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
             else if (o.prec == NMF_PREC_TF32)
                 return NMF_E_NOTIMPL;
         }
-        // the finishing launch of the preparation runs beside the cross term
-        // when the NQP epilogue writes the partials and the cross term is the
-        // tensor-core one: the cross term's stream-K plan leaves it SMs
-        L.overlap_prep = L.fuse_prep && mode >= 0;
+        // the tensor-core cross term's stream-K plan leaves the finishing
+        // launch of the preparation its SMs
         if (mode >= 0) {
             int sms = 0, dev = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int cap = L.overlap_prep && sms > 2 * kSideCtas ? sms - kSideCtas : 0;
+            const int cap = L.fuse_prep && sms > 2 * kSideCtas ? sms - kSideCtas : 0;
             L.hw.plan = tc_plan(m, n, r, mode, cap);
             L.hh.plan = tc_plan(n, m, r, mode, cap);
             sw = L.hw.plan.nslices;
             sh = L.hh.plan.nslices;
         }
     }
+    // the preparation beside the cross term: its finishing launch when the NQP
+    // epilogue writes the partials; all of it when the cross term reads the
+    // other factor itself
+    L.overlap_prep = L.fuse_prep;
+    L.overlap_full = !L.fuse_prep && (sparse || mode < 0);
     const size_t pack_b = mode >= 0 ? std::max(tc_pack_bytes(n, r, mode), tc_pack_bytes(m, r, mode)) : 0;
     const size_t bf_b = mode == TC_BF16 ? sizeof(__nv_bfloat16) * (size_t)m * n : 0;
     if (o.objective < 0 || o.objective > 1 || (o.objective == 1 && sparse))
@@ -1237,6 +1250,8 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
         L.S_h = nnls_grid_query(q);
         if (L.S_w < 1 || L.S_h < 1)
             return NMF_E_CUDA;
+    }
+    if (L.overlap_prep || L.overlap_full) {
         if (!h->side)
             CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
         if (!h->ev_fork)
@@ -1250,8 +1265,9 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     CK(cudaEventRecord(e0, s));
     // G_H = Ht^T Ht, Q_W, Qt, d and packed Ht for the first W-update; with
     // overlap_prep its partials are split as the H-update's NQP launch splits
-    // them, since the first W-update's finishing launch sums them again
-    {
+    // them, since the first W-update's finishing launch sums them again; with
+    // overlap_full the first W-update prepares Ht itself
+    if (!L.overlap_full) {
         PrepArgs pa = prep_args(L, Ht, n, L.Gh, hw);
         if (L.overlap_prep)
             pa.slices = L.S_h;
