@@ -217,10 +217,12 @@ nmf_status nmf_objective_direct(nmf_handle h, const nmf_dense *V, const float *W
                                 int r, float alpha_w, float alpha_h, float beta_w, float beta_h,
                                 double *J_dev);
 
-/* KKT residuals of Eq. 2 for one factor, in FP64: with
+/* KKT residuals of Eq. 2 for one factor: with
  * grad_i = Q X_i - C_i + alpha (Q r x r including the L2 term; symmetric, as
  * every Gram is - it is read by columns),
- * out_dev[0] = max |min(X_ij, grad_ij)|, out_dev[1] = max |X_ij grad_ij|. */
+ * out_dev[0] = max |min(X_ij, grad_ij)|, out_dev[1] = max |X_ij grad_ij|.
+ * The sums of Q X_i run in float-float (exact FP32 products, compensated
+ * sums, ~44 bits); the residuals and maxima are FP64.  r <= 128. */
 nmf_status nmf_kkt(nmf_handle h, const float *Q, const float *C, int64_t rows, int r,
                    float alpha, const float *X, double *out_dev);
 

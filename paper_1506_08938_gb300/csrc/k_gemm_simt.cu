@@ -187,6 +187,9 @@ __global__ void k_transpose(const float *__restrict__ A, int64_t rows, int64_t c
     }
 }
 
+
+}  // namespace
+
 int num_sms()
 {
     static int sms = 0;
@@ -199,8 +202,6 @@ int num_sms()
     }
     return sms;
 }
-
-}  // namespace
 
 int gram_splits(int64_t rows)
 {

@@ -2,7 +2,7 @@
 //  * rescale   - anti-lopsided rescaling of the shared Gram (§3.4 Eq. 3)
 //  * objective - J by the trace identity, FP64 (Def. 1; Table 4 reports
 //                1/2||V - WH||^2), with the L1/L2 terms of §3.5
-//  * kkt       - optimality residuals of Eq. 2, FP64
+//  * kkt       - optimality residuals of Eq. 2 (float-float sums, FP64 residuals)
 //  * sumsq     - ||V||_F^2 in FP64 (constant term of the trace identity)
 // All reductions are two-level with a fixed grid and a last-block finish, so
 // their results do not depend on scheduling.
@@ -148,35 +148,107 @@ __global__ void __launch_bounds__(kRedThreads) k_objective(const ObjArgs a)
 // KKT residuals of one factor, FP64.  One warp per row, the row in smem;
 // lane j forms (Q x)_j reading Q by columns (Q symmetric), so for each k the
 // lanes read one contiguous run of Q instead of 32 separate rows.
+// a b added to the float-float sum (hi, lo): the product exactly as p + e
+// (one rounding, recovered by an FMA), p added to hi by Knuth's TwoSum, both
+// error terms to lo.  The _rn intrinsics keep the compiler from contracting
+// or reassociating any of it.
+__device__ __forceinline__ void ff_add_prod(float &hi, float &lo, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bv = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+constexpr int kKktRows = 32;   // rows of X per tile
+constexpr int kKktRowsPerThread = kKktRows / 4;
+
+// Gradient entries grad_ij = alpha - C_ij + sum_k Q_kj X_ik of one tile of
+// 32 rows: thread (ty, tx) owns rows ty*8 .. ty*8+7 and columns tx, tx + 64.
+// The sums run over k in order in float-float (products exact, sums
+// compensated: about 44 bits), i.e. FP64-grade for FP32 data at FP32
+// rates - this part's FP64 pipe runs at 1/64 of the FP32 rate, and a
+// double per operand cost two conversions per product there.  The residuals
+// and their maxima are FP64.
 __global__ void __launch_bounds__(256) k_kkt(const float *__restrict__ Q,
                                              const float *__restrict__ C, int64_t rows, int r,
                                              float alpha, const float *__restrict__ X,
                                              unsigned long long *out)
 {
-    __shared__ float sx[8][kMaxRank];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    extern __shared__ float kkt_smem[];
+    float *Qs = kkt_smem;            // r x r, as Q
+    float *Xs = kkt_smem + r * r;    // kKktRows x r
+    __shared__ double red[2][8];
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    for (int i = threadIdx.x; i < r * r; i += blockDim.x)
+        Qs[i] = Q[i];
+    const bool c0 = tx < r, c1 = tx + 64 < r;
     double m1 = 0.0, m2 = 0.0;
-    for (int64_t row = (int64_t)blockIdx.x * 8 + w; row < rows; row += (int64_t)gridDim.x * 8) {
-        for (int c = lane; c < r; c += 32)
-            sx[w][c] = X[row * r + c];
-        __syncwarp();
-        for (int j = lane; j < r; j += 32) {
-            double gj = (double)alpha - (double)C[row * r + j];
-            for (int k = 0; k < r; ++k)
-                gj += (double)__ldg(Q + k * r + j) * (double)sx[w][k];
-            const double x = (double)sx[w][j];
-            const double a1 = fabs(x < gj ? x : gj), a2 = fabs(x * gj);
-            m1 = a1 > m1 ? a1 : m1;
-            m2 = a2 > m2 ? a2 : m2;
+    const int64_t tiles = (rows + kKktRows - 1) / kKktRows;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t row0 = t * kKktRows;
+        const int nr = rows - row0 < kKktRows ? (int)(rows - row0) : kKktRows;
+        __syncthreads();   // Qs staged; the previous tile's Xs read
+        for (int i = threadIdx.x; i < nr * r; i += blockDim.x)
+            Xs[i] = X[row0 * r + i];
+        for (int i = nr * r + threadIdx.x; i < kKktRows * r; i += blockDim.x)
+            Xs[i] = 0.f;   // rows past the end: finite values, results unused
+        __syncthreads();
+        float hi[kKktRowsPerThread][2], lo[kKktRowsPerThread][2];
+#pragma unroll
+        for (int i = 0; i < kKktRowsPerThread; ++i) {
+            hi[i][0] = hi[i][1] = 0.f;
+            lo[i][0] = lo[i][1] = 0.f;
         }
-        __syncwarp();
+        const float *xr = Xs + ty * kKktRowsPerThread * r;
+        for (int k = 0; k < r; ++k) {
+            const float q0 = c0 ? Qs[k * r + tx] : 0.f;
+            const float q1 = c1 ? Qs[k * r + tx + 64] : 0.f;
+#pragma unroll
+            for (int i = 0; i < kKktRowsPerThread; ++i) {
+                const float xv = xr[i * r + k];   // one address per warp: broadcast
+                ff_add_prod(hi[i][0], lo[i][0], q0, xv);
+                ff_add_prod(hi[i][1], lo[i][1], q1, xv);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kKktRowsPerThread; ++i) {
+            const int lr = ty * kKktRowsPerThread + i;
+            if (lr >= nr)
+                continue;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int j = tx + 64 * c;
+                if (j >= r)
+                    continue;
+                const double g = ((double)hi[i][c] + (double)lo[i][c]) + (double)alpha -
+                                 (double)C[(row0 + lr) * r + j];
+                const double x = (double)xr[i * r + j];
+                const double a1 = fabs(x < g ? x : g), a2 = fabs(x * g);
+                m1 = a1 > m1 ? a1 : m1;
+                m2 = a2 > m2 ? a2 : m2;
+            }
+        }
     }
     // non-negative doubles order like their bit patterns
     for (int o = 16; o > 0; o >>= 1) {
         m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
         m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
     }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
+        red[0][w] = m1;
+        red[1][w] = m2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < 8; ++q) {
+            m1 = fmax(m1, red[0][q]);
+            m2 = fmax(m2, red[1][q]);
+        }
         atomicMax(out, (unsigned long long)__double_as_longlong(m1));
         atomicMax(out + 1, (unsigned long long)__double_as_longlong(m2));
     }
@@ -449,11 +521,22 @@ cudaError_t launch_kkt(const float *Q, const float *C, int64_t rows, int r, floa
     cudaMemsetAsync(out, 0, 2 * sizeof(double), s);
     if (rows <= 0)
         return cudaGetLastError();
-    int64_t blocks = (rows + 7) / 8;
-    if (blocks > 1024)
-        blocks = 1024;
-    k_kkt<<<(unsigned)blocks, 256, 0, s>>>(Q, C, rows, r, alpha, X,
-                                           reinterpret_cast<unsigned long long *>(out));
+    if (r < 1 || r > kMaxRank)
+        return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(r * r + kKktRows * r) * sizeof(float);
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(k_kkt, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)((kMaxRank * kMaxRank + kKktRows * kMaxRank) *
+                                                         sizeof(float)));
+        if (e != cudaSuccess)
+            return e;
+        attr_set = true;
+    }
+    const int64_t tiles = (rows + kKktRows - 1) / kKktRows;
+    const int64_t cap = 2 * (int64_t)num_sms();
+    k_kkt<<<(unsigned)(tiles < cap ? tiles : cap), 256, smem, s>>>(
+        Q, C, rows, r, alpha, X, reinterpret_cast<unsigned long long *>(out));
     count_launch();
     return cudaGetLastError();
 }

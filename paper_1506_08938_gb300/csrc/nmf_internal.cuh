@@ -99,6 +99,7 @@ struct NnlsArgs {
     bool grid_query;        // host: only compute the grid into *grid_out
 };
 cudaError_t launch_nnls(const NnlsArgs &a, cudaStream_t s);
+int num_sms();   // SMs of the current device (cached)
 int nnls_grid_query(const NnlsArgs &a);   // the grid launch_nnls would use (0 on error)
 cudaError_t prepare_nnls(int r, int lanes);
 bool nnls_layout(int r, int lanes, int *G, int *J);

@@ -296,12 +296,14 @@ def test_objective_trace_identity(h):
     assert abs(J.item() - Jo) / Jo < 1e-6
 
 
-def test_kkt(h):
-    Q, Cm, X0 = nqp_batch(9, 12, 333)
+@pytest.mark.parametrize("r,rows", [(12, 333), (1, 40), (64, 31), (100, 2049), (128, 777)])
+def test_kkt(h, r, rows):
+    # tiles of 32 rows (a ragged last tile), one or two columns per thread
+    Q, Cm, X0 = nqp_batch(9 + r, r, rows)
     out = P.nmf_kkt(h, t32(Q), t32(Cm), t32(X0), alpha=0.02)
     h.sync()
     ko = O.kkt(Q, Cm, 0.02, X0)
-    np.testing.assert_allclose(out.cpu().numpy(), ko, rtol=1e-5)
+    np.testing.assert_allclose(out.cpu().numpy(), ko, rtol=1e-9)
 
 
 def run_solve(h, inst, T, K, eps=0.0, use_graph=False, sparse=None, objective="trace"):
