@@ -9,9 +9,11 @@
 // leaves the partial sum of the row it stops in as a carry; a second kernel
 // adds the carries of each row in piece order, so results are reproducible.
 //
-// Inner loop: the warp loads 32 (column, value) pairs at once, then for each
-// pair gathers the r-float row B[col] with lane-strided, coalesced loads and
-// accumulates in FP32 registers (lane l owns columns l, l+32, ...).
+// Inner loop: the warp loads 32 (column, value) pairs at once, then gathers
+// the r-float rows B[col] of eight pairs at a time with lane-strided,
+// coalesced loads (the gathers are latency-bound: eight rows in flight per
+// lane) and accumulates them in pair order in FP32 registers (lane l owns
+// columns l, l+32, ...).
 #include "nmf_internal.cuh"
 
 namespace nmfi {
@@ -45,7 +47,36 @@ __device__ __forceinline__ int64_t mp_search(const int64_t *__restrict__ rowptr,
     return lo;
 }
 
-// acc += sum_{k in [kb, ke)} vals[k] * B[colidx[k], :]
+// acc += the pairs q .. q+U-1 of the warp's 32 (col, val): U gathers of B
+// rows in flight per lane before their FMAs, which run in pair order
+template <int U, int J>
+__device__ __forceinline__ void gather_pairs(int col, float val, int q,
+                                             const float *__restrict__ B, int r, int lane,
+                                             float (&acc)[J])
+{
+    const float *b[U];
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        b[u] = B + (int64_t)__shfl_sync(kFull, col, q + u) * r;
+        v[u] = __shfl_sync(kFull, val, q + u);
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        int c = lane + 32 * j;
+        if (c < r) {
+            float x[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                x[u] = __ldg(b[u] + c);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                acc[j] = fmaf(v[u], x[u], acc[j]);
+        }
+    }
+}
+
+// acc += sum_{k in [kb, ke)} vals[k] * B[colidx[k], :], in k order
 template <int J, typename VT>
 __device__ __forceinline__ void accumulate(const int32_t *__restrict__ colidx,
                                            const VT *__restrict__ vals, int64_t kb, int64_t ke,
@@ -61,37 +92,14 @@ __device__ __forceinline__ void accumulate(const int32_t *__restrict__ colidx,
             val = to_f<VT>(vals[k + lane]);
         }
         int q = 0;
-        for (; q + 4 <= n; q += 4) {
-            int c0 = __shfl_sync(kFull, col, q), c1 = __shfl_sync(kFull, col, q + 1);
-            int c2 = __shfl_sync(kFull, col, q + 2), c3 = __shfl_sync(kFull, col, q + 3);
-            float v0 = __shfl_sync(kFull, val, q), v1 = __shfl_sync(kFull, val, q + 1);
-            float v2 = __shfl_sync(kFull, val, q + 2), v3 = __shfl_sync(kFull, val, q + 3);
-            const float *b0 = B + (int64_t)c0 * r, *b1 = B + (int64_t)c1 * r;
-            const float *b2 = B + (int64_t)c2 * r, *b3 = B + (int64_t)c3 * r;
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                int c = lane + 32 * j;
-                if (c < r) {
-                    float x0 = __ldg(b0 + c), x1 = __ldg(b1 + c), x2 = __ldg(b2 + c),
-                          x3 = __ldg(b3 + c);
-                    acc[j] = fmaf(v0, x0, acc[j]);
-                    acc[j] = fmaf(v1, x1, acc[j]);
-                    acc[j] = fmaf(v2, x2, acc[j]);
-                    acc[j] = fmaf(v3, x3, acc[j]);
-                }
-            }
+        for (; q + 8 <= n; q += 8)
+            gather_pairs<8, J>(col, val, q, B, r, lane, acc);
+        if (q + 4 <= n) {
+            gather_pairs<4, J>(col, val, q, B, r, lane, acc);
+            q += 4;
         }
-        for (; q < n; ++q) {
-            int c0 = __shfl_sync(kFull, col, q);
-            float v0 = __shfl_sync(kFull, val, q);
-            const float *b0 = B + (int64_t)c0 * r;
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                int c = lane + 32 * j;
-                if (c < r)
-                    acc[j] = fmaf(v0, __ldg(b0 + c), acc[j]);
-            }
-        }
+        for (; q < n; ++q)
+            gather_pairs<1, J>(col, val, q, B, r, lane, acc);
     }
 }
 
@@ -156,13 +164,44 @@ __global__ void k_spmm_fixup(const int64_t *__restrict__ carry_row,
     const int64_t R = carry_row[t];
     if (R >= rows || (t > 0 && carry_row[t - 1] == R))
         return;
+    // the run [t, end) of pieces carrying row R (carry rows never decrease
+    // along the pieces), found 32 entries at a time
+    int64_t end = t + 1;
+    for (;;) {
+        const int64_t u = end + lane;
+        const unsigned other = __ballot_sync(kFull, !(u < pieces && carry_row[u] == R));
+        if (other) {
+            end += __ffs(other) - 1;
+            break;
+        }
+        end += 32;
+    }
     float acc[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) {
         int c = lane + 32 * j;
         acc[j] = c < r ? C[R * r + c] : 0.f;
     }
-    for (int64_t u = t; u < pieces && carry_row[u] == R; ++u) {
+    // the carries in piece order, eight loaded ahead of their adds (a Zipf
+    // head row of V^T spans hundreds of pieces)
+    constexpr int U = 8;
+    int64_t u = t;
+    for (; u + U <= end; u += U) {
+        float v[U][J];
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                int c = lane + 32 * j;
+                v[q][j] = c < r ? carry_val[(u + q) * r + c] : 0.f;
+            }
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+                acc[j] += v[q][j];
+    }
+    for (; u < end; ++u) {
 #pragma unroll
         for (int j = 0; j < J; ++j) {
             int c = lane + 32 * j;
