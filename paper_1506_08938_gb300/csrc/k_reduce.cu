@@ -255,93 +255,141 @@ __global__ void __launch_bounds__(256) k_kkt(const float *__restrict__ Q,
 }
 
 // J = 1/2 sum_ij (V_ij - W_i . Ht_j)^2 + penalties, the residual formed
-// element by element: W_i . Ht_j by an FP32 fma chain over r, its square
-// summed in FP32 over the thread's 16 elements of a 64 x 64 tile, the tile
-// sums in FP64.  Avoids the cancellation of the trace identity.  Persistent
-// CTAs walk the tiles; FP64 arithmetic (a small fraction of FP32 throughput
-// on this part) is kept to one add per thread per tile.  A thread owns a
-// 4 x 4 block (rows ty*4.., columns tx*4..), read from the staged factors as
-// one 16-byte load each per k (rows padded to 68 floats: 16-byte aligned,
-// at most 4-way conflicts while staging).
-__global__ void __launch_bounds__(256) k_objective_direct(const ObjDirectArgs a)
+// element by element: W_i . Ht_j by an FP32 fma chain over r in order, its
+// square summed in FP32 over the thread's 64 elements of a 128 x 128 tile,
+// the tile sums in FP64.  Avoids the cancellation of the trace identity.
+// One persistent CTA per SM walks the tiles (8 x 8 elements a thread: 64
+// FMAs per four 16-byte shared loads); FP64 arithmetic (a small fraction of
+// FP32 throughput on this part) is kept to one add per thread per tile.
+// Thread (ty, tx) owns rows {ty*4 + i, 64 + ty*4 + i} and columns
+// {tx*4 + j, 64 + tx*4 + j} of the tile, so consecutive threads read
+// consecutive 16-byte words of the staged factors.  The factors' rows of a
+// tile go to shared memory (k-major, 64 columns of r per stage) by cp.async,
+// two stages deep: the next stage's copies land while this one is computed.
+constexpr int kObjTile = 128, kObjKc = 64, kObjLd = kObjTile + 4;
+constexpr size_t kObjSmem = 2 * 2 * kObjKc * kObjLd * sizeof(float);
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid)
 {
-    constexpr int BT = 64, KC = 32, LD = BT + 4;
-    __shared__ __align__(16) float Ws[KC][LD];
-    __shared__ __align__(16) float Hs[KC][LD];
+    // src-size 0 fills the word with zeros and reads nothing
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(256, 1) k_objective_direct(const ObjDirectArgs a)
+{
+    constexpr int BT = kObjTile, KC = kObjKc, LD = kObjLd;
+    extern __shared__ __align__(16) float obj_smem[];
     __shared__ double sh[32];
     __shared__ bool last;
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int r = a.r;
     const int64_t tiles_n = (a.n + BT - 1) / BT;
     const int64_t tiles = ((a.m + BT - 1) / BT) * tiles_n;
-    double fit = 0.0;
-    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int nch = (r + KC - 1) / KC;   // stages per tile
+    const bool v_vec = (a.ldv & 3) == 0 && (reinterpret_cast<uintptr_t>(a.V) & 15) == 0;
+    // stage st of this CTA: tile blockIdx.x + (st / nch) gridDim.x, chunk st % nch
+    const int64_t my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t stages = my_tiles * nch;
+    auto stage_copy = [&](int64_t st) {
+        const int64_t tile = blockIdx.x + (st / nch) * gridDim.x;
+        const int k0 = (int)(st % nch) * KC;
         const int64_t i0 = (tile / tiles_n) * BT, j0 = (tile % tiles_n) * BT;
-        // this thread's 16 elements of V, requested now and used after the
-        // products: the loads are in flight while the tile is computed
-        float vv[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int64_t gi = i0 + ty * 4 + i, gj = j0 + tx * 4 + j;
-                vv[i][j] = (gi < a.m && gj < a.n) ? a.V[gi * a.ldv + gj] : 0.f;
-            }
-        float acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                acc[i][j] = 0.f;
-        for (int k0 = 0; k0 < a.r; k0 += KC) {
-            constexpr int PER = BT * KC / 256;
-            float wv[PER], hv[PER];
-#pragma unroll
-            for (int q = 0; q < PER; ++q) {   // every load before the first store
-                const int idx = tid + q * 256, rr = idx / KC, kk = idx % KC;
-                const int64_t gi = i0 + rr, gj = j0 + rr;
-                const int gk = k0 + kk;
-                wv[q] = (gi < a.m && gk < a.r) ? a.W[gi * a.r + gk] : 0.f;
-                hv[q] = (gj < a.n && gk < a.r) ? a.Ht[gj * a.r + gk] : 0.f;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const int idx = tid + q * 256, rr = idx / KC, kk = idx % KC;
-                Ws[kk][rr] = wv[q];
-                Hs[kk][rr] = hv[q];
-            }
-            __syncthreads();
-            const int kc = a.r - k0 < KC ? a.r - k0 : KC;   // columns of this chunk
+        float *Ws = obj_smem + (st & 1) * 2 * KC * LD, *Hs = Ws + KC * LD;
+        // element (row rr, column kk) of the stage: consecutive threads take
+        // consecutive columns of one row (coalesced), stored k-major
 #pragma unroll 4
-            for (int kk = 0; kk < kc; ++kk) {
-                const float4 w4 = *reinterpret_cast<const float4 *>(&Ws[kk][ty * 4]);
-                const float4 h4 = *reinterpret_cast<const float4 *>(&Hs[kk][tx * 4]);
-                const float w[4] = {w4.x, w4.y, w4.z, w4.w};
-                const float hh[4] = {h4.x, h4.y, h4.z, h4.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        acc[i][j] = fmaf(w[i], hh[j], acc[i][j]);
-            }
+        for (int idx = tid; idx < BT * KC; idx += 256) {
+            const int rr = idx / KC, kk = idx % KC;
+            const int gk = k0 + kk;
+            const int64_t gi = i0 + rr, gj = j0 + rr;
+            const bool wv = gi < a.m && gk < r, hv = gj < a.n && gk < r;
+            cp_async4(&Ws[kk * LD + rr], wv ? a.W + gi * r + gk : a.W, wv);
+            cp_async4(&Hs[kk * LD + rr], hv ? a.Ht + gj * r + gk : a.Ht, hv);
         }
-        float f32 = 0.f;
+    };
+    double fit = 0.0;
+    float vv[8][8], acc[8][8];
+    if (stages > 0)
+        stage_copy(0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int64_t st = 0; st < stages; ++st) {
+        if (st + 1 < stages)
+            stage_copy(st + 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");   // stage st has landed
+        __syncthreads();
+        const int64_t tile = blockIdx.x + (st / nch) * gridDim.x;
+        const int c = (int)(st % nch);
+        const int64_t i0 = (tile / tiles_n) * BT, j0 = (tile % tiles_n) * BT;
+        if (c == 0) {
+            // this thread's 64 elements of V, requested now and used after
+            // the products: the loads are in flight while the tile is computed
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            int64_t gi = i0 + ty * 4 + i;
-            if (gi >= a.m)
-                continue;
+            for (int i = 0; i < 8; ++i) {
+                const int64_t gi = i0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                int64_t gj = j0 + tx * 4 + j;
-                if (gj < a.n) {
-                    float e = vv[i][j] - acc[i][j];
-                    f32 = fmaf(e, e, f32);
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t gj = j0 + h * 64 + tx * 4;
+                    if (gi < a.m && v_vec && gj + 3 < a.n) {
+                        const float4 q = *reinterpret_cast<const float4 *>(a.V + gi * a.ldv + gj);
+                        vv[i][h * 4 + 0] = q.x;
+                        vv[i][h * 4 + 1] = q.y;
+                        vv[i][h * 4 + 2] = q.z;
+                        vv[i][h * 4 + 3] = q.w;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            vv[i][h * 4 + j] =
+                                (gi < a.m && gj + j < a.n) ? a.V[gi * a.ldv + gj + j] : 0.f;
+                    }
                 }
             }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    acc[i][j] = 0.f;
         }
-        fit += (double)f32;
+        const float *Ws = obj_smem + (st & 1) * 2 * KC * LD, *Hs = Ws + KC * LD;
+        const int kc = r - c * KC < KC ? r - c * KC : KC;   // columns of this stage
+#pragma unroll 2
+        for (int kk = 0; kk < kc; ++kk) {
+            const float4 wa = *reinterpret_cast<const float4 *>(Ws + kk * LD + ty * 4);
+            const float4 wb = *reinterpret_cast<const float4 *>(Ws + kk * LD + 64 + ty * 4);
+            const float4 ha = *reinterpret_cast<const float4 *>(Hs + kk * LD + tx * 4);
+            const float4 hb = *reinterpret_cast<const float4 *>(Hs + kk * LD + 64 + tx * 4);
+            const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+            const float hh[8] = {ha.x, ha.y, ha.z, ha.w, hb.x, hb.y, hb.z, hb.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    acc[i][j] = fmaf(w[i], hh[j], acc[i][j]);
+        }
+        if (c == nch - 1) {
+            float f32 = 0.f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int64_t gi = i0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+                if (gi >= a.m)
+                    continue;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int64_t gj = j0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+                    if (gj < a.n) {
+                        const float e = vv[i][j] - acc[i][j];
+                        f32 = fmaf(e, e, f32);
+                    }
+                }
+            }
+            fit += (double)f32;
+        }
+        __syncthreads();   // this buffer is refilled two stages on
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     // penalty sums over the factors: FP32 groups of 16, FP64 across groups
     double sw = 0.0, sw2 = 0.0, shh = 0.0, sh2 = 0.0;
     {
@@ -499,17 +547,27 @@ cudaError_t launch_objective(const ObjArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-constexpr int kObjBlocks = 4 * 152;   // persistent CTAs of the direct objective
+constexpr int kObjBlocks = 4 * 152;   // most persistent CTAs of the direct objective (partials)
 
 size_t objective_direct_partials(int64_t, int64_t) { return (size_t)kObjBlocks * 5; }
 
 cudaError_t launch_objective_direct(const ObjDirectArgs &a, cudaStream_t s)
 {
     ProfScope prof_(KC_OBJECTIVE, s);
-    const int64_t tiles = ((a.m + 63) / 64) * ((a.n + 63) / 64);
+    const int64_t tiles = ((a.m + kObjTile - 1) / kObjTile) * ((a.n + kObjTile - 1) / kObjTile);
     if (tiles <= 0)
         return cudaErrorInvalidValue;
-    k_objective_direct<<<(unsigned)(tiles < kObjBlocks ? tiles : kObjBlocks), 256, 0, s>>>(a);
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_objective_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kObjSmem);
+        if (e != cudaSuccess)
+            return e;
+        attr_set = true;
+    }
+    int64_t grid = num_sms();   // one CTA per SM (64 accumulators a thread)
+    grid = grid < kObjBlocks ? grid : kObjBlocks;
+    k_objective_direct<<<(unsigned)(tiles < grid ? tiles : grid), 256, kObjSmem, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }

@@ -330,8 +330,11 @@ def f32_inst(inst):
     return inst
 
 
-def test_objective_direct_matches_oracle(h):
-    inst = f32_inst(WL.tiny(seed=3, r=8, m=300, n=200))
+@pytest.mark.parametrize("r,m,n", [(8, 300, 200), (37, 257, 203), (64, 129, 130)])
+def test_objective_direct_matches_oracle(h, r, m, n):
+    # 128 x 128 tiles with ragged edges; n % 4 != 0 takes the scalar loads of V;
+    # r > 16 spans several staged chunks of the factors
+    inst = f32_inst(WL.tiny(seed=3 + r, r=r, m=m, n=n))
     Jo = O.objective_dense(inst.V, inst.W0, inst.Ht0, 0.1, 0.2, 0.3, 0.4)
     J = P.nmf_objective_direct(h, t32(inst.V), t32(inst.W0), t32(inst.Ht0), 0.1, 0.2, 0.3, 0.4)
     h.sync()
