@@ -835,9 +835,10 @@ nmf_status enqueue_objective(nmf_handle h, Loop &L, const nmf_solve_opts &o, dou
         CK(launch_objective_direct(b, h->stream));
         return NMF_OK;
     }
-    // J(W, H) by the FP64 trace identity.  With overlap_prep G_H = Ht^T Ht is
-    // finished at the start of the next W-update; finish it now for the
-    // objective (the next W-update's finishing launch writes the same values)
+    // J(W, H) by the FP64 trace identity.  With the preparation beside the
+    // cross term (overlap_prep, overlap_full) G_H = Ht^T Ht is completed at
+    // the start of the next W-update; complete it now for the objective (the
+    // next W-update writes the same values again)
     if (L.overlap_prep)
         CK(launch_prep_finish(finish_args(L, L.hw, L.Gh), L.S_h, h->stream));
     else if (L.overlap_full)
