@@ -252,6 +252,14 @@ __host__ __device__ __forceinline__ float rn_tf32(float v)
 #endif
 }
 
+// The same for an operand the tensor core reads as TF32: it drops the low 13
+// bits itself (as it does for A, whose raw FP32 bits it reads as the high
+// part), so adding half a TF32 ulp is all the rounding needs
+__device__ __forceinline__ float rn_tf32_operand(float v)
+{
+    return __uint_as_float(__float_as_uint(v) + 0x1000u);
+}
+
 // CTA that owns iteration x when `iters` iterations are cut into `grid`
 // contiguous ranges [floor(c iters/grid), floor((c+1) iters/grid)).
 __host__ __device__ inline int owner_of(int64_t x, int64_t iters, int grid)
@@ -557,10 +565,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const float4 v = *reinterpret_cast<const float4 *>(ar + 16 * (c ^ (row & 7)));
-                r[4 * c + 0] = __float_as_uint(rn_tf32(v.x - __uint_as_float(__float_as_uint(v.x) & 0xffffe000u)));
-                r[4 * c + 1] = __float_as_uint(rn_tf32(v.y - __uint_as_float(__float_as_uint(v.y) & 0xffffe000u)));
-                r[4 * c + 2] = __float_as_uint(rn_tf32(v.z - __uint_as_float(__float_as_uint(v.z) & 0xffffe000u)));
-                r[4 * c + 3] = __float_as_uint(rn_tf32(v.w - __uint_as_float(__float_as_uint(v.w) & 0xffffe000u)));
+                r[4 * c + 0] = __float_as_uint(rn_tf32_operand(v.x - __uint_as_float(__float_as_uint(v.x) & 0xffffe000u)));
+                r[4 * c + 1] = __float_as_uint(rn_tf32_operand(v.y - __uint_as_float(__float_as_uint(v.y) & 0xffffe000u)));
+                r[4 * c + 2] = __float_as_uint(rn_tf32_operand(v.z - __uint_as_float(__float_as_uint(v.z) & 0xffffe000u)));
+                r[4 * c + 3] = __float_as_uint(rn_tf32_operand(v.w - __uint_as_float(__float_as_uint(v.w) & 0xffffe000u)));
             }
             tmem_st32(tmem + lane_addr + LO_COL0 + w.lo * 32, r);
             tmem_wait_st();
@@ -651,10 +659,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int q = 0; q < (int)(kABytes / 16 / kEpi); ++q) {
                     const float4 v = a4[t + kEpi * q];
                     float4 r;
-                    r.x = rn_tf32(v.x - __uint_as_float(__float_as_uint(v.x) & 0xffffe000u));
-                    r.y = rn_tf32(v.y - __uint_as_float(__float_as_uint(v.y) & 0xffffe000u));
-                    r.z = rn_tf32(v.z - __uint_as_float(__float_as_uint(v.z) & 0xffffe000u));
-                    r.w = rn_tf32(v.w - __uint_as_float(__float_as_uint(v.w) & 0xffffe000u));
+                    r.x = rn_tf32_operand(v.x - __uint_as_float(__float_as_uint(v.x) & 0xffffe000u));
+                    r.y = rn_tf32_operand(v.y - __uint_as_float(__float_as_uint(v.y) & 0xffffe000u));
+                    r.z = rn_tf32_operand(v.z - __uint_as_float(__float_as_uint(v.z) & 0xffffe000u));
+                    r.w = rn_tf32_operand(v.w - __uint_as_float(__float_as_uint(v.w) & 0xffffe000u));
                     l4[t + kEpi * q] = r;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
