@@ -1,8 +1,9 @@
-"""Row-sharded outer iteration (the multi-GPU schedule) on two gloo ranks on
+"""Row-sharded outer iteration (the multi-GPU schedule) on two and three gloo ranks on
 the CPU, with the FP64 oracle supplying the arithmetic: the concatenated
 W blocks and the replicated Ht must equal the unsharded oracle run up to
-summation order (the exchanged Gram and cross term are sums of two partial
-sums instead of one), and both ranks must hold the same Ht bit for bit."""
+summation order (the exchanged Gram and cross term are sums of per-rank
+partial sums instead of one), and every rank must hold the same Ht bit for
+bit."""
 import os
 import socket
 import tempfile
@@ -77,14 +78,16 @@ def test_row_block_partition():
             assert max(sizes) - min(sizes) <= 1
 
 
-def test_two_ranks_match_unsharded_oracle():
+@pytest.mark.parametrize("world", [2, 3])
+def test_ranks_match_unsharded_oracle(world):
+    # 61 rows over 3 ranks: uneven blocks (21, 20, 20)
     import torch.multiprocessing as mp
-    world = 2
     with tempfile.TemporaryDirectory() as d:
         mp.spawn(worker, args=(world, free_port(), d), nprocs=world, join=True)
         Ws = [np.load(os.path.join(d, f"W{p}.npy")) for p in range(world)]
         Hs = [np.load(os.path.join(d, f"H{p}.npy")) for p in range(world)]
-    assert np.array_equal(Hs[0], Hs[1])
+    for p in range(1, world):
+        assert np.array_equal(Hs[0], Hs[p])
     inst = instance()
     Wo, Ho, _, _ = O.nmf_solve(inst.W0, inst.Ht0, T, V=inst.V, beta_w=BETA, beta_h=BETA,
                                opts=O.nqp_opts(max_inner=K, eps=0.0))
