@@ -59,8 +59,8 @@ typedef enum { NMF_F32 = 0, NMF_BF16 = 1, NMF_F64 = 2 } nmf_dtype;
  *  FP32       FP32-accurate: on tcgen05 tensor cores each operand is split
  *             into a TF32-exact high part and its remainder and
  *             hi*hi + hi*lo + lo*hi is accumulated in FP32 (relative error
- *             ~1e-6 like FP32); falls back to FP32_SIMT when the data's row
- *             pitch is not a multiple of 16 bytes.
+ *             ~1e-7, as FP32 summation); falls back to FP32_SIMT when the
+ *             data's row pitch is not a multiple of 16 bytes.
  *  TF32       operands truncated to TF32 (10-bit mantissa), FP32 accumulate.
  *  BF16       operands rounded to BF16, FP32 accumulate (the solve keeps a
  *             BF16 copy of V and V^T on the device).
