@@ -33,6 +33,15 @@ MUTANTS = {
     "cd_column_wrong": ("g[i] += Q[i * r + p] * dp;", "g[i] += Q[i * r + i] * dp;"),
     "cross_index_swapped": ("s += A[i * lda + t] * B[t * r + j];", "s += A[i * lda + t] * B[j * r + t % r];"),
     "tie_break_highest": ("if (gain > best) {", "if (gain >= best && gain > 0.0) {"),
+    # the structure of Alg. 3's repeat loop
+    "line_search_unmasked_gradient": (
+        "gb[i] = (!dead[i] && (y[i] > 0.0 || g[i] < 0.0)) ? g[i] : 0.0;",
+        "gb[i] = !dead[i] ? g[i] : 0.0;"),
+    "line_search_half_step": ("double alpha = s / den;", "double alpha = 0.5 * s / den;"),
+    "line_search_not_projected": ("yn[i] = v > 0.0 ? v : 0.0;", "yn[i] = v;"),
+    "cd_step_not_projected": ("double di = (v > 0.0 ? v : 0.0) - y[i];", "double di = v - y[i];"),
+    "cd_one_step_per_iteration": ("int T = o->cd_steps < 0 ? r : o->cd_steps;",
+                                  "int T = o->cd_steps < 0 ? 1 : o->cd_steps;"),
 }
 
 PINS = [
