@@ -42,6 +42,10 @@ MUTANTS = {
     "cd_step_not_projected": ("double di = (v > 0.0 ? v : 0.0) - y[i];", "double di = v - y[i];"),
     "cd_one_step_per_iteration": ("int T = o->cd_steps < 0 ? r : o->cd_steps;",
                                   "int T = o->cd_steps < 0 ? 1 : o->cd_steps;"),
+    # the outer loop (Alg. 1/2): the H-update's Gram and cross term
+    "m_step_keeps_e_step_gram": ("        oracle_gram(W, m, r, o->beta_h, Q);\n", "\n"),
+    "m_step_cross_reads_v": ("oracle_cross_dense(VT, n, m, m, W, r, CH);",
+                             "oracle_cross_dense(Vd, n, m, m, W, r, CH);"),
 }
 
 PINS = [
@@ -57,6 +61,8 @@ PINS = [
     T.test_stop_rule_stops_at_first_qualifying_iteration,
     T.test_diagonal_q_one_iteration_exact,
     T.test_nqp_kkt_at_convergence,
+    T.test_outer_objective_monotone_tiny,
+    T.test_exact_low_rank_recovery,
 ]
 
 
