@@ -46,6 +46,10 @@ MUTANTS = {
     "m_step_keeps_e_step_gram": ("        oracle_gram(W, m, r, o->beta_h, Q);\n", "\n"),
     "m_step_cross_reads_v": ("oracle_cross_dense(VT, n, m, m, W, r, CH);",
                              "oracle_cross_dense(Vd, n, m, m, W, r, CH);"),
+    # the objective (Def. 1, Table 4's 1/2) and the KKT residual (Eq. 2)
+    "objective_drops_half": ("return 0.5 * fit + aw * l1w", "return fit + aw * l1w"),
+    "objective_csr_cross_sign": ("0.5 * (vv - 2.0 * vwh + whwh)", "0.5 * (vv + 2.0 * vwh + whwh)"),
+    "kkt_l1_sign": ("double gj = -C[i * r + j] + alpha;", "double gj = -C[i * r + j] - alpha;"),
 }
 
 PINS = [
@@ -63,6 +67,7 @@ PINS = [
     T.test_nqp_kkt_at_convergence,
     T.test_outer_objective_monotone_tiny,
     T.test_exact_low_rank_recovery,
+    T.test_objectives_agree_and_match_numpy,
 ]
 
 
