@@ -50,6 +50,11 @@ MUTANTS = {
     "objective_drops_half": ("return 0.5 * fit + aw * l1w", "return fit + aw * l1w"),
     "objective_csr_cross_sign": ("0.5 * (vv - 2.0 * vwh + whwh)", "0.5 * (vv + 2.0 * vwh + whwh)"),
     "kkt_l1_sign": ("double gj = -C[i * r + j] + alpha;", "double gj = -C[i * r + j] - alpha;"),
+    # the plain definitions: Gram X^T X and the CSR cross term
+    "gram_outer_index": ("s += X[k * r + i] * X[k * r + j];", "s += X[k * r + i] * X[k * r + i];"),
+    "csr_cross_row_end": ("for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)\n                s += vals[p] * B",
+                          "for (int64_t p = rowptr[i]; p + 1 < rowptr[i + 1]; ++p)\n                s += vals[p] * B"),
+    "csr_objective_drops_square": ("vv += vals[p] * vals[p];", "vv += vals[p];"),
 }
 
 PINS = [
@@ -68,6 +73,7 @@ PINS = [
     T.test_outer_objective_monotone_tiny,
     T.test_exact_low_rank_recovery,
     T.test_objectives_agree_and_match_numpy,
+    T.test_sparse_solve_equals_dense_solve,
 ]
 
 
