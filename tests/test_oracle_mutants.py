@@ -55,6 +55,7 @@ MUTANTS = {
     "csr_cross_row_end": ("for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)\n                s += vals[p] * B",
                           "for (int64_t p = rowptr[i]; p + 1 < rowptr[i + 1]; ++p)\n                s += vals[p] * B"),
     "csr_objective_drops_square": ("vv += vals[p] * vals[p];", "vv += vals[p];"),
+    "rescale_diagonal_unscaled": ("Qt[i * r + j] = 1.0;   /* Q_ii", "Qt[i * r + j] = H[i * r + j];   /* Q_ii"),
 }
 
 PINS = [
