@@ -66,6 +66,8 @@ def load(path: str):
     L.oracle_rescale.argtypes = [_P, C.c_int, _P, _P, _P]
     L.oracle_nqp.argtypes = [_P, _P, C.c_int, _P, C.POINTER(NqpOpts), _P, _P]
     L.oracle_nqp.restype = C.c_int
+    L.oracle_nqp_min_gap.argtypes = [_P, _P, C.c_int, _P, C.POINTER(NqpOpts), C.c_double, _P]
+    L.oracle_nqp_min_gap.restype = C.c_int
     L.oracle_nnls_update.argtypes = [_P, _P, C.c_int64, C.c_int, C.c_double, _P,
                                      C.POINTER(NqpOpts), C.c_double, _P, _P]
     L.oracle_nnls_update.restype = C.c_int64
@@ -157,6 +159,32 @@ def nqp(H, h, x0, opts: NqpOpts | None = None, maxstop=None):
     if maxstop is None:
         return x, k, sf.value
     return x, k, sf.value, ms.value
+
+
+def nqp_min_gaps(Q, Cm, alpha, X0, opts: NqpOpts | None = None, tie_units=16.0):
+    """Greedy-choice margins of each row of a half-step (as nnls_update, no
+    fast break), over the row's coordinate steps (see nqp_core in oracle.c):
+    returns (margin, rel_margin, swap) arrays - the smallest gap between the
+    two largest gains in units of the gain difference an FP32 gradient cannot
+    resolve, the smallest gap relative to the best gain, and the largest move
+    |dx_p| + |dx_s| (rescaled variables) of a step whose gap is below
+    tie_units such units.  Instrumentation for the parity tests: a row may
+    legitimately take another coordinate in FP32 only at such a step, and the
+    move swapped there bounds what that choice changes."""
+    Q = _f64(Q)
+    Cm = _f64(Cm)
+    X0 = _f64(X0)
+    rows, r = X0.shape
+    o = opts or nqp_opts()
+    out = np.empty((rows, 3))
+    g = (C.c_double * 3)()
+    for i in range(rows):
+        h = np.ascontiguousarray(-Cm[i] + alpha)
+        x = X0[i].copy()
+        lib().oracle_nqp_min_gap(_ptr(Q), _ptr(h), r, _ptr(x), C.byref(o), float(tie_units),
+                                 C.addressof(g))
+        out[i] = g[:]
+    return out[:, 0], out[:, 1], out[:, 2]
 
 
 def nnls_update(Q, Cm, alpha, X0, opts: NqpOpts | None = None, maxstop_in=0.0):

@@ -152,8 +152,20 @@ static double proj_grad_sq(const double *y, const double *g, const uint8_t *dead
 /* enumeration, Lawson-Hanson, KKT, closed forms); the iteration itself is  */
 /* pinned by the §3.4 worked example (59 plain line-search steps).          */
 /* ---------------------------------------------------------------------- */
-OR_API int oracle_nqp(const double *H, const double *h, int r, double *x,
-                      const oracle_nqp_opts *o, double *maxstop, double *s_final)
+/* min_gap (optional, instrumentation only): over all coordinate steps taken,
+ * the smallest margin between the two largest gains, best - second, in units
+ * of what an FP32 rendering of the same step cannot resolve: a gain D_i moves
+ * by about |dx_i| dg when the gradient entry g_i is off by dg, and an FP32
+ * gradient carries rounding of order dg = 2^-24 G with
+ * G = max_i (|q_i| + sum_j |Q_ij| |y_j|), the size of the terms it is built
+ * from.  min_gap[0] = min (best - second) / ((|dx_p| + |dx_s|) 2^-24 G);
+ * min_gap[1] = min (best - second) / best, the plain relative margin;
+ * min_gap[2] = the largest |dx_p| + |dx_s| over the steps whose margin is
+ * below min_gap[3] such units (the size of a move that an unresolved choice
+ * could have swapped). */
+static int nqp_core(const double *H, const double *h, int r, double *x,
+                    const oracle_nqp_opts *o, double *maxstop, double *s_final,
+                    double *min_gap)
 {
     double *Q = (double *)malloc(sizeof(double) * (size_t)r * r);
     double *buf = (double *)malloc(sizeof(double) * (size_t)r * 7);
@@ -229,7 +241,7 @@ OR_API int oracle_nqp(const double *H, const double *h, int r, double *x,
             /* greedy block coordinate descent */
             for (int t = 0; t < T; ++t) {
                 int p = -1;
-                double best = 0.0, dp = 0.0;
+                double best = 0.0, dp = 0.0, second = 0.0, ds = 0.0;
                 for (int i = 0; i < r; ++i) {
                     if (dead[i])
                         continue;
@@ -238,13 +250,36 @@ OR_API int oracle_nqp(const double *H, const double *h, int r, double *x,
                     double di = (v > 0.0 ? v : 0.0) - y[i];
                     double gain = -(g[i] * di + 0.5 * qii * di * di);
                     if (gain > best) {    /* strict: lowest index wins ties */
+                        second = best;
+                        ds = dp;
                         best = gain;
                         p = i;
                         dp = di;
+                    } else if (gain > second) {
+                        second = gain;
+                        ds = di;
                     }
                 }
                 if (p < 0)
                     break;
+                if (min_gap) {
+                    double G = 0.0;
+                    for (int i = 0; i < r; ++i) {
+                        double s = fabs(q[i]);
+                        for (int j = 0; j < r; ++j)
+                            s += fabs(Q[i * r + j]) * fabs(y[j]);
+                        if (s > G)
+                            G = s;
+                    }
+                    double unit = (fabs(dp) + fabs(ds)) * ldexp(G, -24);
+                    double m0 = unit > 0.0 ? (best - second) / unit : 1e300;
+                    if (m0 < min_gap[0])
+                        min_gap[0] = m0;
+                    if (m0 < min_gap[3] && fabs(dp) + fabs(ds) > min_gap[2])
+                        min_gap[2] = fabs(dp) + fabs(ds);
+                    if ((best - second) / best < min_gap[1])
+                        min_gap[1] = (best - second) / best;
+                }
                 for (int i = 0; i < r; ++i)
                     g[i] += Q[i * r + p] * dp;   /* Q symmetric: column p */
                 y[p] += dp;
@@ -269,6 +304,27 @@ OR_API int oracle_nqp(const double *H, const double *h, int r, double *x,
     free(Q);
     free(buf);
     free(dead);
+    return k;
+}
+
+OR_API int oracle_nqp(const double *H, const double *h, int r, double *x,
+                      const oracle_nqp_opts *o, double *maxstop, double *s_final)
+{
+    return nqp_core(H, h, r, x, o, maxstop, s_final, NULL);
+}
+
+/* Alg. 3 as oracle_nqp, also reporting the margins between the two largest
+ * gains of its coordinate steps described at nqp_core: out[0..2] as
+ * min_gap[0..2] there (1e300, 1 and 0 if it took no step), with the
+ * unresolved-step threshold tie_units in FP32 gain-resolution units. */
+OR_API int oracle_nqp_min_gap(const double *H, const double *h, int r, double *x,
+                              const oracle_nqp_opts *o, double tie_units, double *out)
+{
+    double mg[4] = {1e300, 1.0, 0.0, tie_units};
+    int k = nqp_core(H, h, r, x, o, NULL, NULL, mg);
+    out[0] = mg[0];
+    out[1] = mg[1];
+    out[2] = mg[2];
     return k;
 }
 

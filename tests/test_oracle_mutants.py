@@ -56,6 +56,18 @@ MUTANTS = {
                           "for (int64_t p = rowptr[i]; p + 1 < rowptr[i + 1]; ++p)\n                s += vals[p] * B"),
     "csr_objective_drops_square": ("vv += vals[p] * vals[p];", "vv += vals[p];"),
     "rescale_diagonal_unscaled": ("Qt[i * r + j] = 1.0;   /* Q_ii", "Qt[i * r + j] = H[i * r + j];   /* Q_ii"),
+    # the fast break (maxStop) of Alg. 2/3 in both readings
+    "maxstop_threshold_strict": ("maxstop && sk <= *maxstop)", "maxstop && sk < *maxstop)"),
+    "maxstop_same_half_step": ("double ms = maxstop_in, sf = 0.0;",
+                               "double ms = sm > maxstop_in ? sm : maxstop_in, sf = 0.0;"),
+    "maxstop_other_factor": ("o->nqp.maxstop_mode == 2 ? ms_seq : msw, &ms_next",
+                             "o->nqp.maxstop_mode == 2 ? ms_seq : msh, &ms_next"),
+    "maxstop_previous_update_dropped": ("        else\n            msw = ms_next;",
+                                        "        else\n            msw = 0.0;"),
+    "maxstop_sequential_last_not_max": ("if (o->maxstop_mode == 2 && maxstop && sk > *maxstop)",
+                                        "if (o->maxstop_mode == 2 && maxstop)"),
+    "maxstop_sequential_reset_before_m_step": ("o->nqp.maxstop_mode == 2 ? ms_seq : msh",
+                                               "o->nqp.maxstop_mode == 2 ? 0.0 : msh"),
 }
 
 PINS = [
@@ -75,6 +87,10 @@ PINS = [
     T.test_exact_low_rank_recovery,
     T.test_objectives_agree_and_match_numpy,
     T.test_sparse_solve_equals_dense_solve,
+    T.test_maxstop_mode1_fixed_threshold_rows,
+    T.test_maxstop_mode1_threshold_of_previous_update_same_factor,
+    T.test_maxstop_mode2_running_threshold_row_by_row,
+    T.test_maxstop_mode2_reset_each_outer_iteration_carried_into_m_step,
 ]
 
 
