@@ -64,7 +64,8 @@ typedef enum { NMF_F32 = 0, NMF_BF16 = 1, NMF_F64 = 2 } nmf_dtype;
  *  TF32       operands truncated to TF32 (10-bit mantissa), FP32 accumulate.
  *  BF16       operands rounded to BF16, FP32 accumulate (the solve keeps a
  *             BF16 copy of V and V^T on the device).
- *  BF16X2     reserved (split BF16); not implemented.
+ *  BF16X2     split BF16 (hi + lo): implemented for nmf_gram only (see
+ *             there); nmf_solve and nmf_cross return NMF_E_NOTIMPL.
  *  FP32_SIMT  plain FP32 fused multiply-adds on CUDA cores. */
 typedef enum {
     NMF_PREC_FP32 = 0,
@@ -113,6 +114,12 @@ typedef struct {
     float maxstop;       /* threshold for mode 1 in nmf_nnls_update [0]       */
     int lanes;           /* lanes of a warp per row problem: 1, 2, 4, ..., 32
                             with lanes * 16 >= r; 0 = chosen from r [0]       */
+    int grad_refresh;    /* > 0: every grad_refresh-th repeat-loop iteration of
+                            a row recomputes its gradient Qt y + qt from
+                            scratch instead of carrying it by the updates of
+                            Alg. 3 (the FP32 rounding those accumulate over
+                            hundreds of iterations otherwise shifts the point
+                            a long solve converges to); 0 = off [0]           */
 } nmf_nnls_opts;
 
 /* Options of the outer loop (Alg. 1 / Alg. 2). */
@@ -171,7 +178,15 @@ int64_t nmf_launch_count(void);
 /* Gram matrix Q = X^T X + beta I (r x r, FP32), X rows x r (F32, ld >= r).
  * Alg. 2 "Q = G^T G" (the printed "G G^T" is r x r only as G^T G; §4.2 gives
  * its O(n r^2) cost); beta is the L2 weight of §3.5.  prec selects the
- * product arithmetic (FP32, TF32, BF16, BF16X2). */
+ * operand arithmetic, always with FP32 accumulation on CUDA cores:
+ *   FP32, FP32_SIMT  the stored FP32 values;
+ *   TF32             each element rounded to the nearest TF32 (10-bit mantissa);
+ *   BF16             each element rounded to the nearest BF16 (8-bit mantissa);
+ *   BF16X2           each element split as hi = bf16(x), lo = bf16(x - hi) and
+ *                    hi hi + hi lo + lo hi accumulated (relative error of
+ *                    each product ~2^-16: a Gram from BF16 storage accurate
+ *                    to about FP32 level where conditioning needs it).
+ * nmf_solve forms its Grams from the FP32 factors in FP32 under every prec. */
 nmf_status nmf_gram(nmf_handle h, const nmf_dense *X, float beta, nmf_prec prec, float *Q);
 
 /* Cross term C = V B (V rows x k dense F32/BF16 or CSR with F32/BF16 values;
@@ -348,20 +363,27 @@ nmf_status nmf_server_destroy(nmf_server_t s);
  * plugin code that may not take the driver's allocation path, and callers
  * that cannot create an nmf_handle (whose workspace is allocated).
  *
- * Computes Q = X^T X + beta I exactly like nmf_gram with NMF_PREC_FP32
- * (X rows x r F32 device memory, ld >= r; Q r x r F32 device memory),
- * enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
- * Its split-K partial sums use one fixed device array inside the library
- * (about 4.2 MB, room for 63 partial r x r slices at r <= 128), which every
- * GPU that loads the library holds until the process exits.
+ * Computes Q = X^T X + beta I as nmf_gram with NMF_PREC_FP32 does, equal to
+ * it within FP32 rounding (the sum is split into at most 63 partial sums,
+ * nmf_gram's into up to twice the SM count, so the rounding order differs;
+ * relative Frobenius difference below 2e-6 in the tests).  X is rows x r F32
+ * (ld >= r), Q is r x r F32; both must be device memory of the CURRENT
+ * device, and `cuda_stream` (a cudaStream_t, NULL = legacy default stream)
+ * must belong to it.  rows = 0 gives Q = beta I.  Its split-K partial sums
+ * use one fixed device array inside the library (about 4.2 MB, room for 63
+ * partial r x r slices at r <= 128), which every GPU that loads the library
+ * holds until the process exits.
  *
  * Limits and errors: r > 128 returns NMF_E_SHAPE (the array holds r <= 128);
- * NULL pointers NMF_E_ARG; non-F32 X NMF_E_DTYPE; a failed CUDA call
- * NMF_E_CUDA.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call shares the one array: calls
- * whose work overlaps on the GPU (other streams, other host threads) race
- * and must be serialised by the caller. */
+ * NULL pointers, or X or Q not on the current device, NMF_E_ARG; non-F32 X
+ * NMF_E_DTYPE; a failed CUDA call NMF_E_CUDA.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not use this entry point after a
+ * cudaDeviceReset of that device (the kept address belonged to the context
+ * the reset destroyed).  Every call shares the one array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. */
 nmf_status nmf_gram_noalloc(const nmf_dense *X, float beta, float *Q, void *cuda_stream);
 
 /* ---- instrumentation ------------------------------------------------------- */

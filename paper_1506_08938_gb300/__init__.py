@@ -48,7 +48,8 @@ class Matrix(C.Structure):
 
 class NnlsOpts(C.Structure):
     _fields_ = [("max_inner", C.c_int), ("eps", C.c_double), ("cd_steps", C.c_int),
-                ("maxstop_mode", C.c_int), ("maxstop", C.c_float), ("lanes", C.c_int)]
+                ("maxstop_mode", C.c_int), ("maxstop", C.c_float), ("lanes", C.c_int),
+                ("grad_refresh", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -221,9 +222,9 @@ def matrix_csr(rowptr, colidx, vals, ncols: int) -> Matrix:
 
 
 def nnls_opts(max_inner=50, eps=1e-3, cd_steps=-1, maxstop_mode=0, maxstop=0.0,
-              lanes=0) -> NnlsOpts:
+              lanes=0, grad_refresh=0) -> NnlsOpts:
     return NnlsOpts(int(max_inner), float(eps), int(cd_steps), int(maxstop_mode), float(maxstop),
-                    int(lanes))
+                    int(lanes), int(grad_refresh))
 
 
 def solve_opts(outer_iters, rel_gap_target=0.0, f_star=0.0, alpha_w=0.0, alpha_h=0.0,
@@ -291,15 +292,22 @@ def nmf_gram(h: Handle, X, beta=0.0, prec="fp32", Q=None):
 
 def nmf_gram_noalloc(X, beta=0.0, Q=None, stream=None):
     """Gram without any allocation inside the library (no handle needed); Q
-    must be preallocated by the caller when it cannot allocate either."""
+    must be preallocated by the caller when it cannot allocate either.  The
+    call runs with X's device current; Q and the stream must belong to it."""
     import torch
     _need_cuda(X)
     r = X.shape[1]
     Q = Q if Q is not None else torch.empty(r, r, device=X.device, dtype=torch.float32)
-    stream = stream if stream is not None else torch.cuda.current_stream(X.device)
-    d = dense(X)
-    _check(lib().nmf_gram_noalloc(C.byref(d), float(beta), _ptr(Q),
-                                  C.c_void_p(stream.cuda_stream)), "nmf_gram_noalloc")
+    if Q.shape != (r, r) or Q.dtype != torch.float32 or Q.device != X.device or \
+            not Q.is_contiguous():
+        raise ValueError("Q must be a contiguous (r, r) float32 tensor on X's device")
+    with torch.cuda.device(X.device):
+        stream = stream if stream is not None else torch.cuda.current_stream(X.device)
+        if stream.device != X.device:
+            raise ValueError("the stream must belong to X's device")
+        d = dense(X)
+        _check(lib().nmf_gram_noalloc(C.byref(d), float(beta), _ptr(Q),
+                                      C.c_void_p(stream.cuda_stream)), "nmf_gram_noalloc")
     return Q
 
 

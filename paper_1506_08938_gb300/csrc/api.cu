@@ -61,6 +61,12 @@ thread_local bool tl_prof_off = false;
 
 void prof_suspend(bool on) { g_prof.suspended += on ? 1 : -1; }
 void prof_thread_off() { tl_prof_off = true; }
+bool prof_thread_set_off(bool off)
+{
+    const bool was = tl_prof_off;
+    tl_prof_off = off;
+    return was;
+}
 
 void prof_mark(int cls, cudaStream_t s, bool begin)
 {
@@ -280,6 +286,7 @@ NMF_API void nmf_nnls_opts_default(nmf_nnls_opts *o)
     o->maxstop_mode = 0;
     o->maxstop = 0.f;
     o->lanes = 0;
+    o->grad_refresh = 0;
 }
 
 NMF_API int64_t nmf_launch_count(void) { return g_launches.load(); }
@@ -383,8 +390,9 @@ namespace {
 nmf_status gram_into(nmf_handle h, const float *X, int64_t rows, int64_t ld, int r,
                      nmf_prec prec, float *P, int S, float *G)
 {
-    (void)prec;
-    CK(launch_gram_partial(X, rows, ld, r, P, S, h->stream));
+    const int mode = prec == NMF_PREC_TF32 ? GM_TF32 : prec == NMF_PREC_BF16 ? GM_BF16
+                     : prec == NMF_PREC_BF16X2 ? GM_BF16X2 : GM_FP32;
+    CK(launch_gram_partial(X, rows, ld, r, P, S, h->stream, mode));
     CK(launch_sum_slices(P, S, (int64_t)r * r, G, h->stream));
     return NMF_OK;
 }
@@ -400,7 +408,7 @@ NMF_API nmf_status nmf_gram(nmf_handle h, const nmf_dense *X, float beta, nmf_pr
     if (X->dt != NMF_F32)
         return NMF_E_DTYPE;
     if (prec < NMF_PREC_FP32 || prec > NMF_PREC_FP32_SIMT)
-        return NMF_E_ARG;   // every precision computes the Gram in FP32
+        return NMF_E_ARG;
     const int r = (int)X->cols;
     const int S = gram_splits(X->rows);
     Sizer z;
@@ -515,7 +523,7 @@ NMF_API nmf_status nmf_nnls_update(nmf_handle h, const float *Qt, const float *d
     if (rows < 0 || bad_r(r))
         return NMF_E_SHAPE;
     nmf_nnls_opts o = opts_or_default(opts);
-    if (o.maxstop_mode < 0 || o.maxstop_mode > 1)
+    if (o.maxstop_mode < 0 || o.maxstop_mode > 1 || o.grad_refresh < 0)
         return NMF_E_ARG;
     int lg = 0, lj = 0;
     if (!nnls_layout(r, o.lanes, &lg, &lj))
@@ -536,6 +544,7 @@ NMF_API nmf_status nmf_nnls_update(nmf_handle h, const float *Qt, const float *d
     a.maxstop_mode = o.maxstop_mode;
     a.maxstop = o.maxstop;
     a.lanes = o.lanes;
+    a.grad_refresh = o.grad_refresh;
     a.iters = inner_iters;
     a.status = h->status;
     CK(launch_nnls(a, h->stream));
@@ -761,6 +770,7 @@ nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, float *G, HalfStep &
     a.maxstop_mode = L.nn.maxstop_mode;
     a.maxstop = 0.f;
     a.lanes = L.nn.lanes;
+    a.grad_refresh = L.nn.grad_refresh;
     a.iter_total = h->ctr;
     a.status = h->status;
     if (L.nn.maxstop_mode == 1) {
@@ -996,6 +1006,8 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     Loop L{};
     L.r = r;
     L.nn = opts_or_default(&o.nnls);
+    if (L.nn.grad_refresh < 0)
+        return NMF_E_ARG;
     if (L.nn.maxstop_mode < 0 || L.nn.maxstop_mode > 1)
         return NMF_E_NOTIMPL;   // mode 2 (sequential, order-dependent) is the oracle's only
     {

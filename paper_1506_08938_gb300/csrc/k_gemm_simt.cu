@@ -84,14 +84,32 @@ __global__ void __launch_bounds__(kThreads) k_cross_f32(const float *__restrict_
     }
 }
 
+// TF32 value nearest to x (ties to even): keep the sign, the exponent and the
+// top 10 of the 23 stored mantissa bits.  Inf and NaN pass unchanged.
+__device__ __forceinline__ float round_tf32(float x)
+{
+    unsigned u = __float_as_uint(x);
+    if ((u & 0x7f800000u) == 0x7f800000u)
+        return x;
+    u += 0xfffu + ((u >> 13) & 1u);
+    return __uint_as_float(u & 0xffffe000u);
+}
+
 // ---- Gram: P[s] = X[rows(s)]^T X[rows(s)] ---------------------------------
-template <int NB>
+// Operand arithmetic MODE (a GramMode): FP32 as stored; TF32 or BF16 (each
+// element rounded to nearest, products accumulated in FP32); BF16X2 (each
+// element split into hi = bf16(x) and lo = bf16(x - hi), and
+// hi_a hi_b + hi_a lo_b + lo_a hi_b accumulated in FP32, the lo lo term of
+// order 2^-18 dropped).
+template <int NB, int MODE>
 __global__ void __launch_bounds__(kThreads) k_gram_f32(const float *__restrict__ X, int64_t rows,
                                                         int64_t ld, int r, float *__restrict__ P,
                                                         int64_t chunk)
 {
     constexpr int BK = 32, T = NB / 16;
+    constexpr int NL = MODE == GM_BF16X2 ? BK : 1;
     __shared__ float Xs[BK][NB];
+    __shared__ float Xl[NL][NB];          // low parts (BF16X2 only)
     const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
     const int64_t kb = (int64_t)blockIdx.x * chunk;
     const int64_t ke = kb + chunk < rows ? kb + chunk : rows;
@@ -105,7 +123,17 @@ __global__ void __launch_bounds__(kThreads) k_gram_f32(const float *__restrict__
         for (int idx = tid; idx < BK * NB; idx += kThreads) {
             int kk = idx / NB, c = idx - kk * NB;
             int64_t gk = k0 + kk;
-            Xs[kk][c] = (c < r && gk < ke) ? X[gk * ld + c] : 0.f;
+            float v = (c < r && gk < ke) ? X[gk * ld + c] : 0.f;
+            if (MODE == GM_TF32) {
+                v = round_tf32(v);
+            } else if (MODE == GM_BF16) {
+                v = __bfloat162float(__float2bfloat16_rn(v));
+            } else if (MODE == GM_BF16X2) {
+                const float hi = __bfloat162float(__float2bfloat16_rn(v));
+                Xl[kk % NL][c] = __bfloat162float(__float2bfloat16_rn(v - hi));
+                v = hi;
+            }
+            Xs[kk][c] = v;
         }
         __syncthreads();
 #pragma unroll 4
@@ -117,11 +145,27 @@ __global__ void __launch_bounds__(kThreads) k_gram_f32(const float *__restrict__
 #pragma unroll
             for (int b = 0; b < T; ++b)
                 xb[b] = Xs[kk][tj + 16 * b];
+            if (MODE == GM_BF16X2) {
+                float la[T], lb[T];
 #pragma unroll
-            for (int a = 0; a < T; ++a)
+                for (int a = 0; a < T; ++a)
+                    la[a] = Xl[kk % NL][ti + 16 * a];
 #pragma unroll
                 for (int b = 0; b < T; ++b)
-                    acc[a][b] = fmaf(xa[a], xb[b], acc[a][b]);
+                    lb[b] = Xl[kk % NL][tj + 16 * b];
+#pragma unroll
+                for (int a = 0; a < T; ++a)
+#pragma unroll
+                    for (int b = 0; b < T; ++b)
+                        acc[a][b] = fmaf(xa[a], xb[b], fmaf(xa[a], lb[b], fmaf(la[a], xb[b],
+                                                                               acc[a][b])));
+            } else {
+#pragma unroll
+                for (int a = 0; a < T; ++a)
+#pragma unroll
+                    for (int b = 0; b < T; ++b)
+                        acc[a][b] = fmaf(xa[a], xb[b], acc[a][b]);
+            }
         }
         __syncthreads();
     }
@@ -226,8 +270,20 @@ int cross_splits(int64_t M, int64_t K)
     return s < 1 ? 1 : (int)s;
 }
 
+template <int MODE>
+void gram_launch(const float *X, int64_t rows, int64_t ld, int r, float *P, int64_t chunk,
+                 int grid, cudaStream_t s)
+{
+    if (r <= 32)
+        k_gram_f32<32, MODE><<<grid, kThreads, 0, s>>>(X, rows, ld, r, P, chunk);
+    else if (r <= 64)
+        k_gram_f32<64, MODE><<<grid, kThreads, 0, s>>>(X, rows, ld, r, P, chunk);
+    else
+        k_gram_f32<128, MODE><<<grid, kThreads, 0, s>>>(X, rows, ld, r, P, chunk);
+}
+
 cudaError_t launch_gram_partial(const float *X, int64_t rows, int64_t ld, int r, float *P,
-                                int nsplit, cudaStream_t s)
+                                int nsplit, cudaStream_t s, int mode)
 {
     ProfScope prof_(KC_GRAM, s);
     if (rows <= 0) {
@@ -239,14 +295,18 @@ cudaError_t launch_gram_partial(const float *X, int64_t rows, int64_t ld, int r,
     int grid = (int)((rows + chunk - 1) / chunk);
     if (grid < 1)
         grid = 1;
-    if (grid < nsplit)   // trailing slices would stay unwritten: clear them
-        cudaMemsetAsync(P + (int64_t)grid * r * r, 0, sizeof(float) * r * r * (nsplit - grid), s);
-    if (r <= 32)
-        k_gram_f32<32><<<grid, kThreads, 0, s>>>(X, rows, ld, r, P, chunk);
-    else if (r <= 64)
-        k_gram_f32<64><<<grid, kThreads, 0, s>>>(X, rows, ld, r, P, chunk);
-    else
-        k_gram_f32<128><<<grid, kThreads, 0, s>>>(X, rows, ld, r, P, chunk);
+    if (grid < nsplit) {   // trailing slices would stay unwritten: clear them
+        cudaError_t e = cudaMemsetAsync(P + (int64_t)grid * r * r, 0,
+                                        sizeof(float) * r * r * (nsplit - grid), s);
+        if (e != cudaSuccess)
+            return e;
+    }
+    switch (mode) {
+    case GM_TF32: gram_launch<GM_TF32>(X, rows, ld, r, P, chunk, grid, s); break;
+    case GM_BF16: gram_launch<GM_BF16>(X, rows, ld, r, P, chunk, grid, s); break;
+    case GM_BF16X2: gram_launch<GM_BF16X2>(X, rows, ld, r, P, chunk, grid, s); break;
+    default: gram_launch<GM_FP32>(X, rows, ld, r, P, chunk, grid, s); break;
+    }
     count_launch();
     return cudaGetLastError();
 }
@@ -264,8 +324,12 @@ cudaError_t launch_cross_dense_f32(const float *A, int64_t M, int64_t K, int64_t
     int gy = (int)((K + kchunk - 1) / kchunk);
     if (gy < 1)
         gy = 1;
-    if (gy < nsplit)
-        cudaMemsetAsync(P + (int64_t)gy * M * r, 0, sizeof(float) * M * r * (nsplit - gy), s);
+    if (gy < nsplit) {
+        cudaError_t e = cudaMemsetAsync(P + (int64_t)gy * M * r, 0,
+                                        sizeof(float) * M * r * (nsplit - gy), s);
+        if (e != cudaSuccess)
+            return e;
+    }
     dim3 grid((unsigned)((M + 127) / 128), (unsigned)gy);
     if (r <= 32)
         k_cross_f32<32><<<grid, kThreads, 0, s>>>(A, M, K, lda, B, r, P, kchunk);

@@ -582,7 +582,41 @@ __device__ __forceinline__ uint2 nnls_rows(const NnlsArgs &a, const float *__res
         // ---- stop test (Alg. 3): accelerated condition, fast break, cap
         float y[J];
         ld_lane<G, J>(ysg, li, y);
-        const float sk = group_sum<G>(proj_part<J>(y, g));
+        float sk = group_sum<G>(proj_part<J>(y, g));
+        // optional gradient refresh: every grad_refresh-th iteration of a row
+        // the gradient carried by updates is replaced by g = Qt y + qt formed
+        // afresh (qt from the row's C slices again), so that the rounding the
+        // updates accumulate over many iterations does not move the point the
+        // iteration converges to; the stop test then uses the fresh gradient
+        if (a.grad_refresh > 0) {
+            const bool ref = active && (k + 1) % a.grad_refresh == 0;
+            if (__any_sync(kFull, ref)) {
+                float t[J];
+                matvec_rows<G, J>(Qs, ys0, ysg, vb0, t, gi, li, r4);
+                __syncwarp();
+                if (ref) {
+                    const float *cr = a.C + row * r;
+                    float c[J];
+#pragma unroll
+                    for (int j = 0; j < J; ++j)
+                        c[j] = 0.f;
+                    for (int s = 0; s < a.nsplit; ++s) {
+#pragma unroll
+                        for (int j = 0; j < J; ++j) {
+                            const int e = M::coord(li, j);
+                            c[j] += e < r ? cr[(int64_t)s * a.c_stride + e] : 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const int e = M::coord(li, j);
+                        g[j] = ((live >> j) & 1u) ? (a.alpha - c[j]) / sd[e] + t[j] : 0.f;
+                    }
+                }
+                const float s2 = group_sum<G>(proj_part<J>(y, g));
+                sk = ref ? s2 : sk;
+            }
+        }
         if (active) {
             ++k;
             const bool stop = sk <= a.eps * s0 || (a.maxstop_mode == 1 && sk <= mstop) ||

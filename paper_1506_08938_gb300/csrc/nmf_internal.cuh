@@ -62,6 +62,7 @@ struct ProfScope {
 };
 void prof_suspend(bool on);   // no events while a stream is being captured
 void prof_thread_off();       // this host thread never records profiler events
+bool prof_thread_set_off(bool off);   // set this thread's flag, return the old one
 
 // ---- NNLS (Alg. 3) --------------------------------------------------------
 struct NnlsArgs {
@@ -85,6 +86,7 @@ struct NnlsArgs {
     unsigned *s_final_max;  // optional: atomicMax of final ||f||^2 bits
     unsigned *status;       // optional device status word
     int lanes;              // lanes per row (0: chosen from r)
+    int grad_refresh;       // > 0: recompute the gradient every that many iterations
     // optional epilogue (standalone kernel only): each CTA writes the Gram
     // partial of its rows of the solved X into slice blockIdx of gram_P (r x r)
     // and, if pack_mode >= 0, their columns of the packed operand; the grid
@@ -136,9 +138,11 @@ cudaError_t launch_prep_finish_narrow(const PrepArgs &a, int S, int ctas, cudaSt
 int prep_slices(int64_t rows);
 
 // ---- Gram / cross term (SIMT FP32) ----------------------------------------
-// partial Gram slices: P[s] = X[k0:k1]^T X[k0:k1], s < nsplit, each r x r.
+// partial Gram slices: P[s] = X[k0:k1]^T X[k0:k1], s < nsplit, each r x r,
+// with the operand arithmetic `mode` (a GramMode)
+enum GramMode { GM_FP32 = 0, GM_TF32 = 1, GM_BF16 = 2, GM_BF16X2 = 3 };
 cudaError_t launch_gram_partial(const float *X, int64_t rows, int64_t ld, int r, float *P,
-                                int nsplit, cudaStream_t s);
+                                int nsplit, cudaStream_t s, int mode = GM_FP32);
 int gram_splits(int64_t rows);
 // partial cross slices: P[s] = A[:, k0:k1] B[k0:k1, :], each M x r.
 cudaError_t launch_cross_dense_f32(const float *A, int64_t M, int64_t K, int64_t lda,

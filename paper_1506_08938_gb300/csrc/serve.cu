@@ -138,6 +138,7 @@ nmf_status launch_batch(nmf_server_s *S, Slot &sl)
     a.eps = (float)S->o.nnls.eps;
     a.cd_steps = S->o.nnls.cd_steps;
     a.lanes = S->o.nnls.lanes;
+    a.grad_refresh = S->o.nnls.grad_refresh;
     if (launch_nnls(a, st) != cudaSuccess)
         return NMF_E_CUDA;
     if (cudaMemcpyAsync(sl.host, H, 4 * (size_t)cols * r, cudaMemcpyDeviceToHost, st) !=
