@@ -3,18 +3,21 @@ oracle.  Shapes cover partial row tiles, K not a multiple of the 32-wide k
 block, every padded width (r -> 16, 32, 64, 128) and stream-K splits where a
 row tile is shared by several CTAs.
 
-Bounds: FP32 (3xTF32 split with the TMEM accumulator drained into FP32
+Bounds, element by element against |A||B| (= A B here: the inputs are
+nonnegative): FP32 (3xTF32 split with the TMEM accumulator drained into FP32
 registers every k block, the small terms in columns of their own; measured
-1.2e-7 at K = 10000) 2e-6 relative;
-TF32 (10-bit mantissa, truncation) ~ 2^-10 per product: 2e-3; BF16 inputs
-rounded to 8 bits: relative 2^-8 per product: 1e-2.
+1.2e-7 norm-wise at K = 10000) 2e-6; TF32 truncates both operands to a 10-bit
+mantissa, so each product is off by less than 2^-9 of itself: 2^-9 + 2e-6;
+BF16 with A already BF16 (the oracle sees the same A) and B rounded to
+nearest BF16 inside the kernel, each product off by at most 2^-9 of itself:
+2^-9 + 2e-6.  These are worst-case bounds, not fits.
 """
 import numpy as np
 import pytest
 
 import oracle as O
 import workloads as WL
-from tests.gpu_common import dev, rel_err, t32, to_np, torch
+from tests.gpu_common import dev, elementwise_ok, rel_err, t32, to_np, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -44,8 +47,8 @@ def test_tc_cross_fp32_split(h, M, K, r):
     h.sync()
     err = rel_err(to_np(Cg), Co)
     bias = float(np.mean((to_np(Cg) - Co) / Co))
-    print(f"tc fp32 M={M} K={K} r={r}: rel {err:.3e} bias {bias:.3e}")
-    assert err < 2e-6
+    worst = elementwise_ok(to_np(Cg), Co, Co, 2e-6)
+    print(f"tc fp32 M={M} K={K} r={r}: rel {err:.3e} bias {bias:.3e} worst {worst:.3f} x bound")
 
 
 @pytest.mark.parametrize("M,K", [(129, 96), (1000, 3008), (4096, 10000)])
@@ -58,8 +61,8 @@ def test_tc_cross_tf32(h, M, K, r):
     Cg = P.nmf_cross(h, t32(A), t32(B), prec="tf32")
     h.sync()
     err = rel_err(to_np(Cg), Co)
-    print(f"tc tf32 M={M} K={K} r={r}: rel {err:.3e}")
-    assert err < 2e-3
+    worst = elementwise_ok(to_np(Cg), Co, Co, 2.0 ** -9 + 2e-6)
+    print(f"tc tf32 M={M} K={K} r={r}: rel {err:.3e} worst {worst:.3f} x bound")
 
 
 @pytest.mark.parametrize("M,K", [(129, 96), (1000, 3008), (4096, 10000)])
@@ -74,8 +77,8 @@ def test_tc_cross_bf16(h, M, K, r):
     Cg = P.nmf_cross(h, Ab, t32(B), prec="bf16")
     h.sync()
     err = rel_err(to_np(Cg), Co)
-    print(f"tc bf16 M={M} K={K} r={r}: rel {err:.3e}")
-    assert err < 1e-2
+    worst = elementwise_ok(to_np(Cg), Co, Co, 2.0 ** -9 + 2e-6)
+    print(f"tc bf16 M={M} K={K} r={r}: rel {err:.3e} worst {worst:.3f} x bound")
 
 
 def test_tc_cross_unaligned_falls_back(h):
@@ -85,7 +88,7 @@ def test_tc_cross_unaligned_falls_back(h):
     Co = O.cross_dense(A.astype(np.float64), B.astype(np.float64))
     Cg = P.nmf_cross(h, t32(A), t32(B), prec="fp32")
     h.sync()
-    assert rel_err(to_np(Cg), Co) < 2e-6
+    elementwise_ok(to_np(Cg), Co, Co, 2e-6)
     with pytest.raises(P.NmfError):
         P.nmf_cross(h, t32(A), t32(B), prec="tf32")
 
