@@ -386,6 +386,22 @@ nmf_status nmf_server_destroy(nmf_server_t s);
  * serialised by the caller. */
 nmf_status nmf_gram_noalloc(const nmf_dense *X, float beta, float *Q, void *cuda_stream);
 
+/* ---- fault injection -------------------------------------------------------- */
+
+/* Host-side fault injection, with no counterpart in the paper: the library
+ * reads the environment variable NMF_FAULT (a comma-separated list of sites)
+ * at each call that can fail there, and fails as if the failure had happened:
+ *   alloc    a workspace allocation fails          -> NMF_E_NOMEM
+ *   admit    the server refuses a request          -> NMF_E_BUSY
+ *   csr      a request's CSR fails validation      -> NMF_E_ARG
+ *   barrier  the persistent batched launch's grid barrier gets a deadline
+ *            that has already passed: its bounded wait runs out and the
+ *            call returns NMF_E_TIMEOUT through the device status word,
+ *            the context stays usable (the next call resets the barrier)
+ * Nothing injected traps, faults or hangs the GPU.  Returns 1 when `site` is
+ * armed now, else 0. */
+int nmf_fault_armed(const char *site);
+
 /* ---- instrumentation ------------------------------------------------------- */
 
 /* Kernel classes for nmf_profile_read. */

@@ -125,6 +125,8 @@ def _load():
     L.nmf_server_stats.argtypes = [_P, C.POINTER(ServerStats)]
     L.nmf_server_destroy.argtypes = [_P]
     L.nmf_peak_fp32.argtypes = [C.POINTER(C.c_double)]
+    L.nmf_fault_armed.argtypes = [C.c_char_p]
+    L.nmf_fault_armed.restype = C.c_int
     L.nmf_profile_enable.argtypes = [C.c_int]
     L.nmf_profile_read.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     return L

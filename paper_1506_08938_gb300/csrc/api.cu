@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <vector>
@@ -16,6 +17,24 @@ using namespace nmfi;
 namespace nmfi {
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+bool fault_armed(const char *site)
+{
+    const char *env = getenv("NMF_FAULT");
+    if (!env || !site || !*site)
+        return false;
+    const size_t n = strlen(site);
+    for (const char *p = env; *p;) {
+        const char *q = strchr(p, ',');
+        const size_t len = q ? (size_t)(q - p) : strlen(p);
+        if (len == n && strncmp(p, site, n) == 0)
+            return true;
+        if (!q)
+            break;
+        p = q + 1;
+    }
+    return false;
+}
 
 // ---- profiler: pairs of events per kernel class --------------------------
 namespace {
@@ -197,6 +216,8 @@ nmf_status ensure_ws(nmf_handle h, size_t bytes)
 {
     if (bytes <= h->ws_cap)
         return NMF_OK;
+    if (fault_armed("alloc"))
+        return NMF_E_NOMEM;
     CK(cudaStreamSynchronize(h->stream));
     if (h->ws)
         cudaFree(h->ws);
@@ -290,6 +311,8 @@ NMF_API void nmf_nnls_opts_default(nmf_nnls_opts *o)
 }
 
 NMF_API int64_t nmf_launch_count(void) { return g_launches.load(); }
+
+NMF_API int nmf_fault_armed(const char *site) { return fault_armed(site) ? 1 : 0; }
 
 NMF_API nmf_status nmf_create(nmf_handle *out, int device, void *cuda_stream)
 {
@@ -1518,6 +1541,9 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
     ba.status = h->status;
     ba.bar_count = reinterpret_cast<unsigned *>(h->idev + 2);
     ba.bar_gen = reinterpret_cast<unsigned *>(h->idev + 3);
+    // the barrier's bounded wait: 2 s, or a deadline already passed when the
+    // "barrier" fault is injected (the wait runs out, NMF_E_TIMEOUT follows)
+    ba.barrier_ns = fault_armed("barrier") ? 0ull : 2000000000ull;
     CK(cudaMemsetAsync(h->ctr + 1, 0, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(h->idev + 2, 0, 2 * sizeof(int), s));
 

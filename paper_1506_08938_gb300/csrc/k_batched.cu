@@ -27,7 +27,7 @@ constexpr int kT = 256;            // threads per CTA
 constexpr int kWarps = kT / 32;
 constexpr int kGramRows = 256;     // rows of X per Gram item
 constexpr int kCrossRows = 128;    // rows of A per cross item
-constexpr unsigned long long kBarrierNs = 2000000000ull;
+constexpr unsigned long long kBarrierNs = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ unsigned long long gtime()
 {
@@ -36,9 +36,10 @@ __device__ __forceinline__ unsigned long long gtime()
     return t;
 }
 
-// bounded sense-reversing grid barrier; false on timeout
+// bounded sense-reversing grid barrier; false on timeout (a CTA that has to
+// wait gives up after `limit_ns` of global time)
 __device__ bool grid_barrier(unsigned *count, volatile unsigned *gen, unsigned nblocks,
-                             unsigned *status)
+                             unsigned *status, unsigned long long limit_ns)
 {
     __shared__ int ok;
     __syncthreads();
@@ -54,7 +55,7 @@ __device__ bool grid_barrier(unsigned *count, volatile unsigned *gen, unsigned n
             // a barrier that another CTA gave up on never completes: leave
             // at once instead of waiting out the limit again
             const volatile unsigned *vs = status;
-            const unsigned long long dl = gtime() + kBarrierNs;
+            const unsigned long long dl = gtime() + limit_ns;
             while (*gen == g) {
                 if ((*vs & kStTimeout) || gtime() > dl) {
                     atomicOr(status, kStTimeout);
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(kT, 2) k_batched_iter(const BatchArgs a)
         const int64_t hi = a.inst_begin >= 0 ? off[a.inst_begin + 1] : off[a.count];
         run_phase(a, phase, lo + blockIdx.x, hi, gridDim.x, smem);
         if (phase + 1 < a.phase_end) {
-            if (!grid_barrier(a.bar_count, a.bar_gen, gridDim.x, a.status))
+            if (!grid_barrier(a.bar_count, a.bar_gen, gridDim.x, a.status, a.barrier_ns))
                 return;
         }
     }

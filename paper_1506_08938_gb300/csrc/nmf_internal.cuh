@@ -22,6 +22,14 @@ constexpr unsigned kStBadInput = 4u;   // an argument in device memory broke its
 
 void count_launch(int n = 1);
 
+// Host-side fault injection (no counterpart in the paper): true when the
+// comma-separated list in the environment variable NMF_FAULT names `site`.
+// Sites: "alloc" (workspace allocation fails), "admit" (the server refuses
+// admission), "csr" (CSR validation fails), "barrier" (the persistent batched
+// kernel's grid-barrier deadline is zero, so its bounded wait runs out).
+// Nothing here traps or faults the GPU.
+bool fault_armed(const char *site);
+
 // Programmatic dependent launch: a kernel launched with pdl_launch may start
 // (prologue, loads of inputs no earlier kernel writes) while the previous
 // kernel on the stream drains; it must pass pdl_wait() before it reads that
@@ -208,6 +216,7 @@ struct BatchArgs {
     unsigned long long *iter_total;
     unsigned *status;
     unsigned *bar_count, *bar_gen;
+    unsigned long long barrier_ns;   // grid-barrier deadline (kBarrierNs unless injected)
 };
 size_t batched_smem_bytes();
 int64_t batched_items(int phase, int64_t m, int64_t n, int r, int nnls_mult);

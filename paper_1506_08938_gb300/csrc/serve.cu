@@ -298,14 +298,15 @@ NMF_API nmf_status nmf_server_submit(nmf_server_t S, int64_t w, int64_t nnz, con
 {
     if (!S || !rowptr || !out || !ticket || w < 1 || nnz < 0 || (nnz > 0 && (!colidx || !vals)))
         return NMF_E_ARG;
-    if (rowptr[0] != 0 || rowptr[w] != nnz)
+    if (rowptr[0] != 0 || rowptr[w] != nnz || fault_armed("csr"))
         return NMF_E_ARG;
     for (int64_t i = 0; i < nnz; ++i)
         if (colidx[i] < 0 || colidx[i] >= S->wrows)
             return NMF_E_ARG;
     const size_t b = batch_bytes(w, nnz, S->r);
     // a request that could never be admitted is refused up front
-    if (w > S->o.max_batch_cols || b > S->slot_bytes || b > S->o.hbm_budget)
+    if (w > S->o.max_batch_cols || b > S->slot_bytes || b > S->o.hbm_budget ||
+        fault_armed("admit"))
         return NMF_E_BUSY;
     Request q;
     q.w = w;

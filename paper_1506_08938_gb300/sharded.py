@@ -65,15 +65,18 @@ def sharded_iteration(Vp, Vpt, Wp, Ht, ops, opts: ShardOpts, group=None):
     Qw = ops.gram(Ht, opts.beta_w)
     Cw = ops.cross(Vp, Ht)
     Wp = ops.nnls(Qw, Cw, opts.alpha_w, Wp)
-    # H-update: this rank's contributions, summed over ranks in one collective
-    Gp = ops.gram(Wp, 0.0)
+    # H-update: this rank's contributions, summed over ranks in one collective.
+    # The L2 term enters once, through the first rank's Gram (the library's
+    # Q = X^T X + beta I), so the sum is Q_H = sum_p W_p^T W_p + b_h I.
+    dist_on = dist.is_available() and dist.is_initialized()
+    first = (dist.get_rank(group) if dist_on else 0) == 0
+    Gp = ops.gram(Wp, opts.beta_h if first else 0.0)
     Chp = ops.cross(Vpt, Wp)
     buf = torch.cat([Gp.reshape(-1), Chp.reshape(-1)])
-    if dist.is_available() and dist.is_initialized():
+    if dist_on:
         dist.all_reduce(buf, group=group)
-    G = buf[: r * r].reshape(r, r)
+    Qh = buf[: r * r].reshape(r, r)
     Ch = buf[r * r:].reshape(n, r)
-    Qh = G + opts.beta_h * torch.eye(r, dtype=G.dtype, device=G.device)
     Ht = ops.nnls(Qh, Ch, opts.alpha_h, Ht)
     return Wp, Ht
 

@@ -76,3 +76,19 @@ def test_default_nnls_options(lib):
     o = P.NnlsOpts()
     lib.nmf_nnls_opts_default(C.byref(o))
     assert o.max_inner == 50 and abs(o.eps - 1e-3) < 1e-15 and o.cd_steps == -1
+    assert o.grad_refresh == 0
+
+
+def test_fault_sites_parse_from_the_environment(lib, monkeypatch):
+    """NMF_FAULT is a comma-separated list of injection sites, read at each
+    call (no GPU involved): exact names only, no prefixes."""
+    monkeypatch.delenv("NMF_FAULT", raising=False)
+    assert lib.nmf_fault_armed(b"admit") == 0
+    monkeypatch.setenv("NMF_FAULT", "admit,barrier")
+    assert lib.nmf_fault_armed(b"admit") == 1
+    assert lib.nmf_fault_armed(b"barrier") == 1
+    assert lib.nmf_fault_armed(b"alloc") == 0
+    assert lib.nmf_fault_armed(b"adm") == 0
+    assert lib.nmf_fault_armed(b"") == 0
+    monkeypatch.setenv("NMF_FAULT", "csr")
+    assert lib.nmf_fault_armed(b"csr") == 1 and lib.nmf_fault_armed(b"admit") == 0
