@@ -303,6 +303,48 @@ def batched_measurement(P, torch, dev, h, seed, iters=20, warmup=3):
                     "includes its timed candidate iterations)"}
 
 
+def streamed_measurement(P, torch, dev, h, inst, V, Vt, W0, H0, iters=20, chunk=1024):
+    """The one-pass streamed solve (Alg. 2's E-step accumulation, V read once
+    per outer iteration) on the dense workload, against the two-pass solve
+    (V and V^T each read once per iteration): V in pinned host memory
+    (limited internal memory: two chunk buffers of V on the device, chunks
+    over NVLink-C2C) and V on the device.  ms per outer iteration over
+    `iters` iterations from the seeded start (device events), after one
+    untimed iteration of each."""
+    import numpy as np
+    m, n, r = inst.m, inst.n, inst.r
+    Vh = torch.from_numpy(np.ascontiguousarray(inst.V)).pin_memory()
+
+    def o(T):
+        return P.solve_opts(T, beta_w=inst.beta_w, beta_h=inst.beta_h, check_every=0,
+                            nnls=P.nnls_opts(max_inner=50, eps=1e-3))
+
+    def run(kind, T):
+        W, Ht = W0.clone(), H0.clone()
+        if kind == "two_pass":
+            rep = P.nmf_solve(h, V, W, Ht, o(T), Vt=Vt)
+        else:
+            rep = P.nmf_solve_streamed(h, Vh if kind == "host" else V, W, Ht, o(T), chunk)
+        return rep
+
+    out = {}
+    for kind in ("two_pass", "device_one_pass", "host_one_pass"):
+        run(kind, 1)
+        torch.cuda.synchronize()
+        rep = run(kind, iters)
+        ms = rep.ms_total / max(rep.iters_done, 1)
+        out[kind] = {"ms_per_iter": ms, "kbar": rep.kbar, "J": rep.objective}
+    vbytes = 4.0 * m * n
+    out["host_one_pass"]["c2c_gbs"] = vbytes / (out["host_one_pass"]["ms_per_iter"] * 1e-3) / 1e9
+    out["device_one_pass"]["v_hbm_bytes_per_iter"] = vbytes
+    out["two_pass"]["v_hbm_bytes_per_iter"] = 2 * vbytes
+    del Vh
+    return {"workload": WORKLOAD, "iters": iters, "chunk_rows": chunk, "modes": out,
+            "device_bytes_host_mode": 2 * chunk * n * 4 + 4 * (m + n) * r,
+            "note": "one pass: C_W by tensor cores per chunk, C_H += V_b^T W_b on CUDA "
+                    "cores; trace-identity J; no CUDA graph"}
+
+
 SPARSE_T = 100     # outer iterations of the sparse configuration
 TINY_T = 50        # outer iterations of the tiny configuration
 
@@ -509,6 +551,8 @@ def main():
                     help="skip the many-instance measurement")
     ap.add_argument("--batched-iters", type=int, default=20)
     ap.add_argument("--no-sparse", action="store_true", help="skip the sparse measurement")
+    ap.add_argument("--no-streamed", action="store_true",
+                    help="skip the one-pass streamed-solve measurement")
     ap.add_argument("--no-tiny", action="store_true", help="skip the tiny-configuration measurement")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the TF32 / BF16 time-to-gap variants")
@@ -690,6 +734,8 @@ def main():
     h2d = Vh.numel() * 4 + W0h.numel() * 4 + H0h.numel() * 4
     d2h = Wh.numel() * 4 + Hh.numel() * 4 + 8
 
+    streamed = None if args.no_streamed else streamed_measurement(P, torch, dev, h, inst, V, Vt,
+                                                                  W0, H0)
     serve = None if args.no_serve else serve_measurement(P, torch, dev, args.seed,
                                                              seconds=args.serve_seconds)
     batched = None if args.no_batched else batched_measurement(P, torch, dev, h, args.seed,
@@ -775,6 +821,7 @@ def main():
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "variants": variants,
+        "streamed": streamed,
         "serve": serve,
         "batched": batched,
         "sparse": sparse,

@@ -254,6 +254,31 @@ nmf_status nmf_kkt(nmf_handle h, const float *Q, const float *C, int64_t rows, i
 nmf_status nmf_solve(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt, int r, float *W,
                      float *Ht, const nmf_solve_opts *opts, nmf_report *rep);
 
+/* One-pass alternating solve with V streamed in row chunks (Alg. 2 as
+ * printed in §3.3: while the coefficients F_i of a chunk are solved, the
+ * M-step's inputs Y += F_i V_i^T and H += F_i F_i^T are accumulated, so each
+ * outer iteration reads V once).  For chunk b of `chunk_rows` rows of V:
+ * C_W = V_b Ht (tensor cores when n % 4 == 0, else CUDA cores), the rows of
+ * W_b by Alg. 3, G_W += W_b^T W_b, C_H += V_b^T W_b (CUDA cores, FP32); then
+ * Q_H = G_W + b_h I, every row of Ht against C_H, and J by the FP64 trace
+ * identity after every iteration that obj_hist, rel_gap_target or the last
+ * one asks for.
+ *  V        m x n F32, contiguous (ld = n), in DEVICE or HOST memory.  In host
+ *           memory (pinned for full speed) it is the limited-internal-memory
+ *           mode of §1 / Table 1: the device holds two chunk buffers of V
+ *           (2 chunk_rows n floats), W, Ht and O(r (r + n)) of M-step state;
+ *           chunks are copied on a second stream while the previous chunk is
+ *           computed.  The same chunking gives bitwise the same result
+ *           whether V is on the host or the device.
+ *  W, Ht    DEVICE memory (m x r, n x r): initial factors in, result out.
+ *  opts     outer_iters, rel_gap_target / f_star, penalties and nnls as for
+ *           nmf_solve; prec FP32 or FP32_SIMT (NMF_E_NOTIMPL otherwise);
+ *           maxstop_mode must be 0; check_every, use_graph and objective are
+ *           not used (no CUDA graph: the chunk loop is launched directly).
+ * Synchronises before returning and fills *rep (host). */
+nmf_status nmf_solve_streamed(nmf_handle h, const nmf_dense *V, int r, float *W, float *Ht,
+                              const nmf_solve_opts *opts, int64_t chunk_rows, nmf_report *rep);
+
 /* ---- many independent instances ------------------------------------------ */
 
 /* One NMF instance of a batch (all pointers device memory, row-major F32,

@@ -112,6 +112,8 @@ def _load():
                                        C.c_float, C.c_float, C.c_float, _P]
     L.nmf_solve.argtypes = [_P, C.POINTER(Matrix), C.POINTER(Matrix), C.c_int, _P, _P,
                             C.POINTER(SolveOpts), C.POINTER(Report)]
+    L.nmf_solve_streamed.argtypes = [_P, C.POINTER(Dense), C.c_int, _P, _P,
+                                     C.POINTER(SolveOpts), C.c_int64, C.POINTER(Report)]
     L.nmf_solve_batched.argtypes = [_P, C.c_int, C.POINTER(Instance), C.POINTER(SolveOpts),
                                     C.c_int, C.POINTER(Report)]
     L.nmf_project.argtypes = [_P, _P, _P, _P, C.c_int64, C.c_int, C.POINTER(Csr), _P,
@@ -402,6 +404,21 @@ def nmf_solve(h: Handle, V, W, Ht, opts: SolveOpts, Vt=None, csr_parts=None, csr
     rep = Report()
     _check(lib().nmf_solve(h.h, C.byref(Mv), pt, r, _ptr(W), _ptr(Ht), C.byref(opts),
                            C.byref(rep)), "nmf_solve")
+    return rep
+
+
+def nmf_solve_streamed(h: Handle, V, W, Ht, opts: SolveOpts, chunk_rows: int):
+    """One-pass solve with V streamed in row chunks (Alg. 2's E-step
+    accumulation); V a contiguous float32 tensor on the GPU or in (pinned)
+    host memory, W and Ht on the GPU (updated in place).  Returns the Report."""
+    _need_cuda(W, Ht)
+    if not V.is_contiguous():
+        raise ValueError("V must be contiguous")
+    rep = Report()
+    d = dense(V)
+    _check(lib().nmf_solve_streamed(h.h, C.byref(d), W.shape[1], _ptr(W), _ptr(Ht),
+                                    C.byref(opts), int(chunk_rows), C.byref(rep)),
+           "nmf_solve_streamed")
     return rep
 
 

@@ -14,8 +14,10 @@ constexpr int kThreads = 256;
 // ---- cross term: P[s] = A[:, k-range(s)] B[k-range(s), :] -----------------
 // CTA tile BM x NB (NB = padded r), K step BK.  Thread (ty, tx) of a 16 x 16
 // grid owns rows ty + 16 i (i < BM/16) and columns tx + 16 j (j < NB/16):
-// strided ownership keeps the shared-memory reads conflict-free.
-template <int NB>
+// strided ownership keeps the shared-memory reads conflict-free.  TRANS: A
+// is stored transposed, element (m, k) at A[k * lda + m] (the product
+// V_b^T W_b of a block of rows of V, read along those rows).
+template <int NB, bool TRANS>
 __global__ void __launch_bounds__(kThreads) k_cross_f32(const float *__restrict__ A, int64_t M,
                                                          int64_t K, int64_t lda,
                                                          const float *__restrict__ B, int r,
@@ -36,13 +38,20 @@ __global__ void __launch_bounds__(kThreads) k_cross_f32(const float *__restrict_
             acc[i][j] = 0.f;
 
     for (int64_t k0 = kb; k0 < ke; k0 += BK) {
-        // A tile: BM x BK, each warp reads 2 rows x 16 consecutive k
+        // A tile: BM x BK, each warp reads 2 rows x 16 consecutive k (or,
+        // transposed, 32 consecutive m of one k)
 #pragma unroll
         for (int t = 0; t < BM * BK / kThreads; ++t) {
             int idx = tid + t * kThreads;
-            int mm = idx >> 4, kk = idx & 15;
-            int64_t gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < ke) ? A[gm * lda + gk] : 0.f;
+            if (TRANS) {
+                int mm = idx & (BM - 1), kk = idx / BM;
+                int64_t gm = m0 + mm, gk = k0 + kk;
+                As[kk][mm] = (gm < M && gk < ke) ? A[gk * lda + gm] : 0.f;
+            } else {
+                int mm = idx >> 4, kk = idx & 15;
+                int64_t gm = m0 + mm, gk = k0 + kk;
+                As[kk][mm] = (gm < M && gk < ke) ? A[gm * lda + gk] : 0.f;
+            }
         }
 #pragma unroll
         for (int t = 0; t < BK * NB / kThreads; ++t) {
@@ -185,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_gram_f32(const float *__restrict__
 // then warp 0 adds the 8 warp sums in order: a fixed order, so the result is
 // reproducible, with 8 x the loads in flight of one thread per element.
 __global__ void __launch_bounds__(256) k_sum_slices(const float *__restrict__ P, int nsplit,
-                                                    int64_t n, float *__restrict__ out)
+                                                    int64_t n, float *__restrict__ out, bool acc)
 {
     __shared__ float part[8][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(256) k_sum_slices(const float *__restrict__ P,
 #pragma unroll
             for (int q = 0; q < 8; ++q)
                 s += part[q][lane];
-            out[e] = s;
+            out[e] = acc ? out[e] + s : s;
         }
         __syncthreads();
     }
@@ -312,7 +321,8 @@ cudaError_t launch_gram_partial(const float *X, int64_t rows, int64_t ld, int r,
 }
 
 cudaError_t launch_cross_dense_f32(const float *A, int64_t M, int64_t K, int64_t lda,
-                                   const float *B, int r, float *P, int nsplit, cudaStream_t s)
+                                   const float *B, int r, float *P, int nsplit, cudaStream_t s,
+                                   bool trans)
 {
     ProfScope prof_(KC_CROSS, s);
     if (M <= 0)
@@ -331,17 +341,26 @@ cudaError_t launch_cross_dense_f32(const float *A, int64_t M, int64_t K, int64_t
             return e;
     }
     dim3 grid((unsigned)((M + 127) / 128), (unsigned)gy);
-    if (r <= 32)
-        k_cross_f32<32><<<grid, kThreads, 0, s>>>(A, M, K, lda, B, r, P, kchunk);
-    else if (r <= 64)
-        k_cross_f32<64><<<grid, kThreads, 0, s>>>(A, M, K, lda, B, r, P, kchunk);
-    else
-        k_cross_f32<128><<<grid, kThreads, 0, s>>>(A, M, K, lda, B, r, P, kchunk);
+    if (trans) {
+        if (r <= 32)
+            k_cross_f32<32, true><<<grid, kThreads, 0, s>>>(A, M, K, lda, B, r, P, kchunk);
+        else if (r <= 64)
+            k_cross_f32<64, true><<<grid, kThreads, 0, s>>>(A, M, K, lda, B, r, P, kchunk);
+        else
+            k_cross_f32<128, true><<<grid, kThreads, 0, s>>>(A, M, K, lda, B, r, P, kchunk);
+    } else if (r <= 32) {
+        k_cross_f32<32, false><<<grid, kThreads, 0, s>>>(A, M, K, lda, B, r, P, kchunk);
+    } else if (r <= 64) {
+        k_cross_f32<64, false><<<grid, kThreads, 0, s>>>(A, M, K, lda, B, r, P, kchunk);
+    } else {
+        k_cross_f32<128, false><<<grid, kThreads, 0, s>>>(A, M, K, lda, B, r, P, kchunk);
+    }
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_sum_slices(const float *P, int nsplit, int64_t n, float *out, cudaStream_t s)
+cudaError_t launch_sum_slices(const float *P, int nsplit, int64_t n, float *out, cudaStream_t s,
+                              bool accumulate)
 {
     ProfScope prof_(KC_OTHER, s);
     if (n <= 0)
@@ -349,7 +368,7 @@ cudaError_t launch_sum_slices(const float *P, int nsplit, int64_t n, float *out,
     int64_t blocks = (n + 31) / 32;
     if (blocks > 8192)
         blocks = 8192;
-    k_sum_slices<<<(unsigned)blocks, 256, 0, s>>>(P, nsplit, n, out);
+    k_sum_slices<<<(unsigned)blocks, 256, 0, s>>>(P, nsplit, n, out, accumulate);
     count_launch();
     return cudaGetLastError();
 }

@@ -152,13 +152,15 @@ enum GramMode { GM_FP32 = 0, GM_TF32 = 1, GM_BF16 = 2, GM_BF16X2 = 3 };
 cudaError_t launch_gram_partial(const float *X, int64_t rows, int64_t ld, int r, float *P,
                                 int nsplit, cudaStream_t s, int mode = GM_FP32);
 int gram_splits(int64_t rows);
-// partial cross slices: P[s] = A[:, k0:k1] B[k0:k1, :], each M x r.
+// partial cross slices: P[s] = A[:, k0:k1] B[k0:k1, :], each M x r; trans: A
+// is stored as its transpose (element (m, k) at A[k * lda + m])
 cudaError_t launch_cross_dense_f32(const float *A, int64_t M, int64_t K, int64_t lda,
                                    const float *B, int r, float *P, int nsplit,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool trans = false);
 int cross_splits(int64_t M, int64_t K);
-// C = sum of nsplit slices (each n elements)
-cudaError_t launch_sum_slices(const float *P, int nsplit, int64_t n, float *out, cudaStream_t s);
+// C = sum of nsplit slices (each n elements); accumulate: C += that sum
+cudaError_t launch_sum_slices(const float *P, int nsplit, int64_t n, float *out, cudaStream_t s,
+                              bool accumulate = false);
 // out = A^T (A rows x cols, lda) -> cols x rows
 cudaError_t launch_transpose_f32(const float *A, int64_t rows, int64_t cols, int64_t lda,
                                  float *out, cudaStream_t s);
