@@ -13,7 +13,10 @@
 //   C_W,b = V_b Ht       tensor-core cross term (CUDA cores if unaligned)
 //   W_b <- Alg. 3        batched NQPs against Qt_W, d_W
 //   G_W,b = W_b^T W_b    Gram partial slices of the chunk
-//   C_H,b = V_b^T W_b    CUDA-core product read along V_b's rows
+//   C_H,b = V_b^T W_b    tensor cores on a transposed copy of the chunk (it
+//                        stays in L2: V_b is read from HBM or C2C once), or
+//                        CUDA cores reading along V_b's rows when the chunk's
+//                        row count is not a multiple of 4
 // The chunks are independent problems (Alg. 2's parallel loop), so they run
 // side by side; the main stream then sums the C_H,b and the G_W partials in
 // chunk order (the result does not depend on which chunk finished first),
@@ -104,8 +107,9 @@ NMF_API nmf_status nmf_solve_streamed(nmf_handle h, const nmf_dense *V, int r, f
                          ? TC_TF32X3 : -1;
     // ---- workspace
     int max_slices = 1, max_tslices = 1, gw_slices = 0;
-    std::vector<TcPlan> plans(nchunks);
-    std::vector<int> gsl(nchunks), csl(nchunks), goff(nchunks);
+    std::vector<TcPlan> plans(nchunks), tplans(nchunks);
+    std::vector<int> gsl(nchunks), csl(nchunks), goff(nchunks), tsl(nchunks);
+    std::vector<char> ttc(nchunks, 0);   // C_H,b on tensor cores
     for (int b = 0; b < nchunks; ++b) {
         const int64_t rows = std::min(cr, m - (int64_t)b * cr);
         if (mode >= 0) {
@@ -114,8 +118,15 @@ NMF_API nmf_status nmf_solve_streamed(nmf_handle h, const nmf_dense *V, int r, f
         } else {
             csl[b] = cross_splits(rows, n);
         }
+        ttc[b] = mode >= 0 && rows % 4 == 0;
+        if (ttc[b]) {
+            tplans[b] = tc_plan(n, rows, r, mode);
+            tsl[b] = tplans[b].nslices;
+        } else {
+            tsl[b] = cross_splits(n, rows);
+        }
         max_slices = std::max(max_slices, csl[b]);
-        max_tslices = std::max(max_tslices, cross_splits(n, rows));
+        max_tslices = std::max(max_tslices, tsl[b]);
         gsl[b] = gram_splits(rows);
         goff[b] = gw_slices;
         gw_slices += gsl[b];
@@ -126,9 +137,12 @@ NMF_API nmf_status nmf_solve_streamed(nmf_handle h, const nmf_dense *V, int r, f
     for (int k = 0; k < nbufs; ++k)
         z.add<float>((size_t)cr * n);
     z.add<char>(mode >= 0 ? tc_pack_bytes(n, r, mode) : 16);
+    const size_t wpack = mode >= 0 ? tc_pack_bytes(cr, r, mode) : 16;
     for (int w = 0; w < kWorkers; ++w) {
         z.add<float>((size_t)max_slices * cr * r);
         z.add<float>((size_t)max_tslices * n * r);
+        z.add<float>(mode >= 0 ? (size_t)cr * n : 4);   // V_b^T
+        z.add<char>(wpack);                               // packed W_b
     }
     z.add<float>((size_t)nchunks * n * r);
     z.add<float>((size_t)n * r);
@@ -148,10 +162,13 @@ NMF_API nmf_status nmf_solve_streamed(nmf_handle h, const nmf_dense *V, int r, f
     for (int k = 0; k < nbufs; ++k)
         vb[k] = a.take<float>((size_t)cr * n);
     void *pack = a.take<char>(mode >= 0 ? tc_pack_bytes(n, r, mode) : 16);
-    float *Pc[kWorkers], *Pt[kWorkers];
+    float *Pc[kWorkers], *Pt[kWorkers], *VbT[kWorkers];
+    void *packW[kWorkers];
     for (int w = 0; w < kWorkers; ++w) {
         Pc[w] = a.take<float>((size_t)max_slices * cr * r);
         Pt[w] = a.take<float>((size_t)max_tslices * n * r);
+        VbT[w] = a.take<float>(mode >= 0 ? (size_t)cr * n : 4);
+        packW[w] = a.take<char>(wpack);
     }
     float *CHb = a.take<float>((size_t)nchunks * n * r);   // C_H,b of every chunk
     float *CH = a.take<float>((size_t)n * r);
@@ -294,9 +311,16 @@ NMF_API nmf_status nmf_solve_streamed(nmf_handle h, const nmf_dense *V, int r, f
             // the M-step's inputs from this chunk while it is on the device
             CK(launch_gram_partial(W + i0 * r, rows, r, r, Pgw + (size_t)goff[b] * r * r, gsl[b],
                                    ws));
-            const int ts = cross_splits(n, rows);
-            CK(launch_cross_dense_f32(Vb, n, rows, n, W + i0 * r, r, Pt[w], ts, ws, true));
-            CK(launch_sum_slices(Pt[w], ts, n * r, CHb + (size_t)b * n * r, ws));
+            if (ttc[b]) {
+                CK(launch_transpose_f32(Vb, rows, n, n, VbT[w], ws));
+                CK(launch_tc_pack(W + i0 * r, rows, r, mode, packW[w], ws));
+                CK(launch_tc_cross(VbT[w], n, rows, rows, r, mode, packW[w], Pt[w], tplans[b],
+                                   h->status, ws));
+            } else {
+                CK(launch_cross_dense_f32(Vb, n, rows, n, W + i0 * r, r, Pt[w], tsl[b], ws,
+                                          true));
+            }
+            CK(launch_sum_slices(Pt[w], tsl[b], n * r, CHb + (size_t)b * n * r, ws));
             CK(end_chunk(ws));
         }
         for (int w = 0; w < kWorkers; ++w) {
