@@ -490,7 +490,26 @@ def profile_part(part, P, WL, torch, dev, h, seed):
     import ctypes as C
 
     import numpy as np
-    if part == "serve":
+    if part == "nnls":
+        # the NQP launches of the dense workload's two half-steps from the
+        # seeded start, K = 2 fixed inner iterations, three times each
+        inst = WL.dense(seed=seed)
+        V = torch.tensor(inst.V, device=dev)
+        Vt = V.t().contiguous()
+        W0 = torch.tensor(inst.W0, device=dev)
+        H0 = torch.tensor(inst.Ht0, device=dev)
+        o = P.nnls_opts(max_inner=2, eps=0.0)
+        Qtw, dw = P.nmf_rescale(h, P.nmf_gram(h, H0, beta=inst.beta_w))
+        Cw = P.nmf_cross(h, V, H0)
+        Qth, dh = P.nmf_rescale(h, P.nmf_gram(h, W0, beta=inst.beta_h))
+        Ch = P.nmf_cross(h, Vt, W0)
+        for _ in range(3):
+            W = W0.clone()
+            P.nmf_nnls_update(h, Qtw, dw, Cw, W, opts=o)
+            Ht = H0.clone()
+            P.nmf_nnls_update(h, Qth, dh, Ch, Ht, opts=o)
+        h.sync()
+    elif part == "serve":
         wl = WL.serving(seed=seed, rows=SERVE_ROWS, r=SERVE_R, rate=SERVE_RATE, duration=0.5,
                         max_requests=64)
         srv = P.Server(torch.tensor(wl.W, device=dev), slots=8, max_batch_cols=16384,
@@ -562,13 +581,16 @@ def main():
     ap.add_argument("--no-tiny", action="store_true", help="skip the tiny-configuration measurement")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the TF32 / BF16 time-to-gap variants")
-    ap.add_argument("--profile-part", choices=["serve", "batched", "sparse"],
+    ap.add_argument("--profile-part", choices=["serve", "batched", "sparse", "nnls"],
                     help="for ncu: a short run of one measurement (0.5 s of serving, 3 "
-                         "batched iterations, 5 sparse iterations) inside NVTX range "
-                         "'profiled', then exit")
+                         "batched iterations, 5 sparse iterations, or the dense workload's "
+                         "NQP launches at K = 2) inside NVTX range 'profiled' (not nnls), "
+                         "then exit")
     ap.add_argument("--profile", action="store_true",
-                    help="for ncu: 300 warm outer iterations, then 10 inside NVTX range "
-                         "'profiled'; prints per-kernel-class times and exits")
+                    help="for ncu: --profile-warm warm outer iterations, then 10 inside NVTX "
+                         "range 'profiled'; prints per-kernel-class times and exits")
+    ap.add_argument("--profile-warm", type=int, default=300,
+                    help="warm outer iterations before the profiled ones of --profile")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -620,7 +642,7 @@ def main():
     if args.profile:
         W.copy_(W0)
         Ht.copy_(H0)
-        P.nmf_solve(h, V, W, Ht, opts(300, 1e-3, check=0, prec=args.prec), Vt=Vt)
+        P.nmf_solve(h, V, W, Ht, opts(args.profile_warm, 1e-3, check=0, prec=args.prec), Vt=Vt)
         torch.cuda.synchronize()
         P.nmf_profile_enable(True)
         torch.cuda.nvtx.range_push("profiled")
