@@ -318,6 +318,13 @@ nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance *inst,
  * the CUDA-core kernels.  Synchronises the device; allocates a few bytes. */
 nmf_status nmf_peak_fp32(double *tflops);
 
+/* Bandwidth of the sparse cross term's access pattern with its dense operand
+ * resident in L2, in GB/s of gathered data (*gbs, host): warps gather whole
+ * rows of r floats (r <= 128) at hashed indices over a 65536-row table, eight
+ * rows in flight per lane - the roofline of the CSR SpMM, whose factor-row
+ * gathers hit L2.  Synchronises the device; allocates 32 MB at most. */
+nmf_status nmf_peak_l2_gather(int r, double *gbs);
+
 /* ---- projection onto a fixed basis ----------------------------------------- */
 
 /* E-step alone (Alg. 1 E-step, Alg. 2 first loop) against a fixed basis W

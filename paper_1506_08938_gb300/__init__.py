@@ -127,6 +127,7 @@ def _load():
     L.nmf_server_stats.argtypes = [_P, C.POINTER(ServerStats)]
     L.nmf_server_destroy.argtypes = [_P]
     L.nmf_peak_fp32.argtypes = [C.POINTER(C.c_double)]
+    L.nmf_peak_l2_gather.argtypes = [C.c_int, C.POINTER(C.c_double)]
     L.nmf_fault_armed.argtypes = [C.c_char_p]
     L.nmf_fault_armed.restype = C.c_int
     L.nmf_profile_enable.argtypes = [C.c_int]
@@ -141,6 +142,13 @@ def nmf_peak_fp32() -> float:
     """Measured FP32 FFMA throughput of the current device, TFLOP/s."""
     v = C.c_double(0.0)
     _check(lib().nmf_peak_fp32(C.byref(v)), "nmf_peak_fp32")
+    return v.value
+
+
+def nmf_peak_l2_gather(r: int) -> float:
+    """Measured L2-resident gather bandwidth for rows of r floats, GB/s."""
+    v = C.c_double(0.0)
+    _check(lib().nmf_peak_l2_gather(int(r), C.byref(v)), "nmf_peak_l2_gather")
     return v.value
 
 

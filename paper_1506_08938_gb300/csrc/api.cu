@@ -1654,6 +1654,16 @@ NMF_API nmf_status nmf_peak_fp32(double *tflops)
     return NMF_OK;
 }
 
+NMF_API nmf_status nmf_peak_l2_gather(int r, double *gbs)
+{
+    if (!gbs)
+        return NMF_E_ARG;
+    if (bad_r(r))
+        return NMF_E_SHAPE;
+    CK(measure_l2_gather(r, gbs));
+    return NMF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // projection onto a fixed basis
 // ---------------------------------------------------------------------------

@@ -344,4 +344,83 @@ cudaError_t launch_spmm_rowwarp(const int64_t *rowptr, const int32_t *colidx, co
                              s);
 }
 
+// ---- L2 gather roof --------------------------------------------------------
+// The bandwidth of the SpMM's access pattern when its operand is resident in
+// L2: warps gather whole rows of r floats (lane l reads floats l, l + 32, ...)
+// at indices spread over a table that fits L2, eight rows in flight per lane,
+// as the merge-path kernel does.  The indices are a multiplicative hash of the
+// position (a fixed, L2-resident working set; no host randomness).
+namespace {
+
+__global__ void __launch_bounds__(256) k_l2_gather_probe(const float *__restrict__ T, int rows,
+                                                         int r, int64_t n, float *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float acc = 0.f;
+    for (int64_t base = warp * 8; base < n; base += warps * 8) {
+        float v[8][4];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t i = (uint32_t)(base + k);
+            const int row = (int)((i * 2654435761u) % (uint32_t)rows);
+            const float *p = T + (int64_t)row * r;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = lane + 32 * q;
+                v[k][q] = (base + k < n && c < r) ? __ldg(p + c) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                acc += v[k][q];
+    }
+    if (acc == 12345.678f)   // keeps the loads; never true for the zero table
+        out[0] = acc;
+}
+
+}  // namespace
+
+cudaError_t measure_l2_gather(int r, double *gbs)
+{
+    const int rows = 65536;   // 65536 rows of r <= 128 floats: at most 32 MB, inside L2
+    float *T = nullptr, *out = nullptr;
+    cudaError_t e = cudaMalloc(&T, sizeof(float) * (size_t)rows * r);
+    if (e != cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&out, sizeof(float))) != cudaSuccess) {
+        cudaFree(T);
+        return e;
+    }
+    cudaMemset(T, 0, sizeof(float) * (size_t)rows * r);
+    const int64_t n = (int64_t)1 << 22;   // gathered rows per launch
+    const int grid = num_sms() * 8;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int i = 0; i < 2; ++i)   // warm-up: the table into L2, clocks up
+        k_l2_gather_probe<<<grid, 256>>>(T, rows, r, n, out);
+    cudaEventRecord(e0);
+    const int reps = 5;
+    for (int i = 0; i < reps; ++i)
+        k_l2_gather_probe<<<grid, 256>>>(T, rows, r, n, out);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(T);
+    cudaFree(out);
+    if (e != cudaSuccess)
+        return e;
+    if (cudaGetLastError() != cudaSuccess)
+        return cudaErrorLaunchFailure;
+    *gbs = (double)reps * n * r * sizeof(float) / (ms * 1e-3) / 1e9;
+    return cudaSuccess;
+}
+
 }  // namespace nmfi

@@ -116,6 +116,8 @@ bool nnls_layout(int r, int lanes, int *G, int *J);
 
 // FP32 FFMA throughput of this GPU, measured (TFLOP/s)
 cudaError_t measure_fp32_peak(double *tflops);
+// L2-resident row-gather bandwidth for rows of r floats (GB/s of gathered data)
+cudaError_t measure_l2_gather(int r, double *gbs);
 
 // ---- factor preparation (Gram + rescale + tensor-core packing, one launch) --
 struct PrepArgs {

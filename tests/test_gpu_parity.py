@@ -742,3 +742,14 @@ def test_penalty_grid_one_iteration(h, aw, ah, bw, bh):
            bw * nw * nw * ew + bh * nh * nh * eh)
     jb = j_bound(inst, Wo, Ho, ew, eh) * O.objective_dense(inst.V, Wo, Ho) + pen
     assert abs(hist[0] - ho[1]) < max(1e-5 * ho[1], jb)
+
+
+def test_peak_probes(h):
+    """The two measured roofs the benchmark divides by: FP32 FFMA throughput
+    and the L2-resident row-gather bandwidth of the sparse cross term."""
+    tf = P.nmf_peak_fp32()
+    assert 10.0 < tf < 200.0
+    gbs = P.nmf_peak_l2_gather(100)
+    assert 500.0 < gbs < 100000.0
+    with pytest.raises(P.NmfError):
+        P.nmf_peak_l2_gather(129)
