@@ -521,17 +521,58 @@ __device__ __forceinline__ uint2 nnls_rows(const NnlsArgs &a, const float *__res
                     den = fmaf(gb[j], u[j], den);
                 den = group_sum<G>(den);
                 const float al = (s > 0.f && den > 0.f) ? s / den : 0.f;
+                // the projected step; a coordinate the projection clips (its
+                // unprojected value t < 0, so it moves to 0) is counted and,
+                // if it is the group's only one, its correction -t kept
+                unsigned clip = 0;
+                float cval = 0.f;
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
-                    const float yn = fmaxf(0.f, y[j] - al * gb[j]);
+                    const float t = fmaf(-al, gb[j], y[j]);
+                    const float yn = fmaxf(0.f, t);
+                    if (t < 0.f) {
+                        clip |= 1u << j;
+                        cval = -t;
+                    }
                     gb[j] = yn - y[j];   // the step actually taken
                     y[j] = yn;
                 }
                 st_lane<G, J>(ysg, li, y);
-                matvec<G, J>(Qs, vb0, vbg, gb, u, gi, li, r4);
+                // the gradient moves by Qt dy.  With no clipped coordinate
+                // dy = -al gb, so Qt dy = -al u, the product already formed;
+                // with one clipped coordinate p, dy = -al gb + c e_p with c =
+                // -t_p, so Qt dy = -al u + c Qt[:, p].  Only a group whose step
+                // clipped two or more coordinates forms the product of dy.
+                const int nclip = (int)group_sum<G>((float)__popc(clip));
+                const bool full = nclip > 1;
+                if (!full) {
 #pragma unroll
-                for (int j = 0; j < J; ++j)
-                    g[j] += u[j];
+                    for (int j = 0; j < J; ++j)
+                        g[j] = fmaf(-al, u[j], g[j]);
+                }
+                if (__any_sync(kFull, full)) {
+                    matvec<G, J>(Qs, vb0, vbg, gb, u, gi, li, r4);
+                    if (full) {
+#pragma unroll
+                        for (int j = 0; j < J; ++j)
+                            g[j] += u[j];
+                    }
+                }
+                if (__any_sync(kFull, nclip == 1)) {
+                    const unsigned wb = group_bits<G>(__ballot_sync(kFull, clip != 0u), gi);
+                    const int sli = wb ? __ffs(wb) - 1 : 0;
+                    const int src = gi * G + sli;
+                    const int pj = __shfl_sync(kFull, clip ? __ffs(clip) - 1 : 0, src);
+                    const float c = __shfl_sync(kFull, cval, src);
+                    if (nclip == 1) {
+                        const int pc = M::coord(sli, pj);
+                        float col[J];
+                        ld_lane<G, J>(Qs + pc * RP, li, col);
+#pragma unroll
+                        for (int j = 0; j < J; ++j)
+                            g[j] = fmaf(col[j], c, g[j]);
+                    }
+                }
             }
         }
 
