@@ -9,7 +9,9 @@ ragged tail.  Every tolerance is a bound computed from the arithmetic:
   lambda_min(Qt) (tests/gpu_common.py: the solution map is
   1/lambda_min-Lipschitz in the linear term; C = 20, twice the largest
   measured ratio); a fixed-K row may leave it only through a named greedy
-  near-tie (the oracle's gain margin below 2^-10);
+  near-tie: the oracle's best and second gains at some step differ by less
+  than 16 FP32 resolution units of the gain, and the row's error is at most
+  2.5 times the move the swap would make;
 * a default set of well-conditioned problems (kappa(Qt) <= 5) where every
   row's relative error is at most 1e-4, the factor tolerance of the target;
 * norm-wise over a factor, one NNLS solve: <= 16 sqrt(r) kappa u, u = 2^-24;

@@ -350,3 +350,24 @@ def test_chained_one_iteration_solves_equal_one_solve(h):
     P.nmf_solve(h, t32(inst.V), W, Ht, P.solve_opts(T, nnls=nn))
     _, st = gpu_run(h, inst.V, inst.W0, inst.Ht0, T, nn, states=True)
     assert np.array_equal(to_np(W), st[-1][0]) and np.array_equal(to_np(Ht), st[-1][1])
+
+
+def test_checkpoint_resume_is_bitwise(h, tmp_path):
+    """Save after 4 iterations, reload into fresh tensors, run 5 more: the
+    factors equal, bit for bit, those of one 9-iteration solve."""
+    from paper_1506_08938_gb300 import checkpoint as CP
+    inst = f32_inst(WL.tiny(seed=4, r=10))
+    V = t32(inst.V)
+    o = P.solve_opts(9, beta_w=0.05, beta_h=0.05, nnls=P.nnls_opts(max_inner=20, eps=1e-3))
+    W, Ht = t32(inst.W0), t32(inst.Ht0)
+    P.nmf_solve(h, V, W, Ht, o)
+    W1, H1 = t32(inst.W0), t32(inst.Ht0)
+    o4 = P.solve_opts(4, beta_w=0.05, beta_h=0.05, nnls=P.nnls_opts(max_inner=20, eps=1e-3))
+    rep = P.nmf_solve(h, V, W1, H1, o4)
+    path = str(tmp_path / "ckpt.npz")
+    CP.save(path, W1, H1, rep.iters_done, o4)
+    del W1, H1
+    W2, H2, done, meta = CP.load(path)
+    assert done == 4
+    P.nmf_solve(h, V, W2, H2, CP.resume_opts(meta, 9 - done))
+    assert torch.equal(W2, W) and torch.equal(H2, Ht)
