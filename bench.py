@@ -631,7 +631,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16", "fp32_simt"],
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x2", "fp32_simt"],
                     help="cross-term arithmetic of --profile runs")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
@@ -773,7 +773,7 @@ def main():
     reached = all(rp.rel_gap <= GAP for rp in reps)
     inner = sum(rp.inner_total for rp in reps)
 
-    # ---- variants: the same time-to-gap measurement with TF32 and BF16 cross
+    # ---- variants: the same time-to-gap measurement with TF32, BF16 and BF16X2 cross
     # terms, with Alg. 3's maxStop fast break (previous-update reading), and
     # with other accelerated-condition tolerances eps (Alg. 3's stop rule;
     # k-bar as Table 5 defines it) - one warm-up and one timed solve each,
@@ -784,6 +784,8 @@ def main():
                  ("fp32_fastbreak", "fp32", 1, 1e-3)]
         specs += [(f"fp32_eps{e:g}", "fp32", 0, e) for e in (1e-1, 1e-2, 1e-4)]
         specs += [(f"bf16_eps{e:g}", "bf16", 0, e) for e in (1e-1, 1e-2)]
+        specs += [("bf16x2", "bf16x2", 0, 1e-3)]
+        specs += [(f"bf16x2_eps{e:g}", "bf16x2", 0, e) for e in (1e-1, 1e-2)]
         for vp, vprec, vmax, veps in specs:
             vo = opts(8 * T_CONF, veps, target=GAP, fstar=jstar, prec=vprec, maxstop=vmax)
 

@@ -64,8 +64,13 @@ typedef enum { NMF_F32 = 0, NMF_BF16 = 1, NMF_F64 = 2 } nmf_dtype;
  *  TF32       operands truncated to TF32 (10-bit mantissa), FP32 accumulate.
  *  BF16       operands rounded to BF16, FP32 accumulate (the solve keeps a
  *             BF16 copy of V and V^T on the device).
- *  BF16X2     split BF16 (hi + lo): implemented for nmf_gram only (see
- *             there); nmf_solve and nmf_cross return NMF_E_NOTIMPL.
+ *  BF16X2     split BF16 (hi + lo).  Cross term (nmf_cross with BF16 V,
+ *             nmf_solve): V read once rounded to BF16 (as for BF16), the
+ *             factor split as hi = bf16(x), lo = bf16(x - hi), both products
+ *             in one MMA, FP32 accumulate: the factor enters with relative
+ *             error <= 2^-16 instead of BF16's 2^-8, so the NQP's cross term
+ *             stays consistent with its FP32 Gram from one outer iteration to
+ *             the next.  nmf_gram: see there.
  *  FP32_SIMT  plain FP32 fused multiply-adds on CUDA cores. */
 typedef enum {
     NMF_PREC_FP32 = 0,
@@ -180,8 +185,8 @@ int64_t nmf_launch_count(void);
  * its O(n r^2) cost); beta is the L2 weight of §3.5.  prec selects the
  * operand arithmetic, always with FP32 accumulation on CUDA cores:
  *   FP32, FP32_SIMT  the stored FP32 values;
- *   TF32             each element rounded to the nearest TF32 (10-bit mantissa);
- *   BF16             each element rounded to the nearest BF16 (8-bit mantissa);
+ *   TF32             each element rounded to the nearest TF32 (11 significant bits);
+ *   BF16             each element rounded to the nearest BF16 (8 significant bits);
  *   BF16X2           each element split as hi = bf16(x), lo = bf16(x - hi) and
  *                    hi hi + hi lo + lo hi accumulated (relative error of
  *                    each product ~2^-16: a Gram from BF16 storage accurate

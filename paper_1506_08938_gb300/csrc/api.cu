@@ -416,12 +416,12 @@ NMF_API nmf_status nmf_cross(nmf_handle h, const nmf_matrix *V, const float *B, 
     if (d.rows < 0 || d.cols < 0 || d.ld < d.cols || (!d.data && d.rows > 0))
         return NMF_E_SHAPE;
     int mode = -1;
-    if (prec == NMF_PREC_BF16) {
+    if (prec == NMF_PREC_BF16 || prec == NMF_PREC_BF16X2) {
         if (d.dt != NMF_BF16)
             return NMF_E_DTYPE;
-        if (!tc_supported(d.ld, TC_BF16, d.data))
+        mode = prec == NMF_PREC_BF16 ? TC_BF16 : TC_BF16X2;
+        if (!tc_supported(d.ld, mode, d.data))
             return NMF_E_SHAPE;
-        mode = TC_BF16;
     } else if (prec == NMF_PREC_TF32 || prec == NMF_PREC_FP32 || prec == NMF_PREC_FP32_SIMT) {
         if (d.dt != NMF_F32)
             return NMF_E_DTYPE;
@@ -965,7 +965,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     const nmf_solve_opts o = *opts;
     if (o.outer_iters < 0)
         return NMF_E_ARG;
-    if (o.prec < NMF_PREC_FP32 || o.prec > NMF_PREC_FP32_SIMT || o.prec == NMF_PREC_BF16X2)
+    if (o.prec < NMF_PREC_FP32 || o.prec > NMF_PREC_FP32_SIMT)
         return NMF_E_NOTIMPL;
     Loop L{};
     L.r = r;
@@ -1048,10 +1048,10 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     int mode = -1;
     if (!sparse) {
         const int64_t vt_ld_req = Vt ? Vt->d.ld : m;
-        if (o.prec == NMF_PREC_BF16) {
-            if (n % 8 || m % 8 || !tc_supported(n, TC_BF16, V->d.data))
+        if (o.prec == NMF_PREC_BF16 || o.prec == NMF_PREC_BF16X2) {
+            mode = o.prec == NMF_PREC_BF16 ? TC_BF16 : TC_BF16X2;
+            if (n % 8 || m % 8 || !tc_supported(n, mode, V->d.data))
                 return NMF_E_NOTIMPL;
-            mode = TC_BF16;
         } else if (o.prec != NMF_PREC_FP32_SIMT) {
             const int want = o.prec == NMF_PREC_TF32 ? TC_TF32 : TC_TF32X3;
             if (tc_supported(V->d.ld, want, V->d.data) && vt_ld_req % 4 == 0 &&
@@ -1079,7 +1079,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     L.overlap_prep = L.fuse_prep;
     L.overlap_full = !L.fuse_prep && (sparse || mode < 0);
     const size_t pack_b = mode >= 0 ? std::max(tc_pack_bytes(n, r, mode), tc_pack_bytes(m, r, mode)) : 0;
-    const size_t bf_b = mode == TC_BF16 ? sizeof(__nv_bfloat16) * (size_t)m * n : 0;
+    const size_t bf_b = tc_bf16(mode) ? sizeof(__nv_bfloat16) * (size_t)m * n : 0;
     if (o.objective < 0 || o.objective > 1 || (o.objective == 1 && sparse))
         return NMF_E_NOTIMPL;
     L.direct_obj = o.objective == 1;
@@ -1136,7 +1136,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     void *pack = a.take<char>(pack_b);
     __nv_bfloat16 *vbf = a.take<__nv_bfloat16>(bf_b / 2);
     __nv_bfloat16 *vtbf = a.take<__nv_bfloat16>(bf_b / 2);
-    if (mode == TC_BF16) {
+    if (tc_bf16(mode)) {
         // BF16 copies of V and V^T (contiguous), made once per solve
         CK(launch_f32_to_bf16((const float *)V->d.data, m * n, vbf, h->stream));
         if (vt_ld != m)
@@ -1192,10 +1192,10 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     hw.tc_mode = hh.tc_mode = sparse ? -1 : mode;
     hw.pack = hh.pack = pack;
     if (mode >= 0) {
-        hw.Atc = mode == TC_BF16 ? (const void *)vbf : (const void *)hw.A;
-        hw.lda_tc = mode == TC_BF16 ? n : hw.lda;
-        hh.Atc = mode == TC_BF16 ? (const void *)vtbf : (const void *)hh.A;
-        hh.lda_tc = mode == TC_BF16 ? m : hh.lda;
+        hw.Atc = tc_bf16(mode) ? (const void *)vbf : (const void *)hw.A;
+        hw.lda_tc = tc_bf16(mode) ? n : hw.lda;
+        hh.Atc = tc_bf16(mode) ? (const void *)vtbf : (const void *)hh.A;
+        hh.lda_tc = tc_bf16(mode) ? m : hh.lda;
     }
 
     cudaStream_t s = h->stream;

@@ -78,6 +78,11 @@ __device__ __forceinline__ void gram_pack_rows(const PrepArgs &a, float (*Xs)[NB
                 const int64_t o = (int64_t)n * a.kp + gk;
                 if (a.pack_mode == TC_BF16) {
                     reinterpret_cast<__nv_bfloat16 *>(a.pack)[o] = __float2bfloat16_rn(v);
+                } else if (a.pack_mode == TC_BF16X2) {
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                    reinterpret_cast<__nv_bfloat16 *>(a.pack)[o] = hi;
+                    reinterpret_cast<__nv_bfloat16 *>(a.pack)[(int64_t)a.npad * a.kp + o] =
+                        __float2bfloat16_rn(v - __bfloat162float(hi));
                 } else if (a.pack_mode == TC_TF32X3) {
                     const float hi = rn_tf32(v);
                     reinterpret_cast<float *>(a.pack)[o] = hi;
@@ -107,8 +112,11 @@ __device__ __forceinline__ void zero_pack_padding(const PrepArgs &a)
     const int64_t padk = a.kp - a.rows;
     for (int64_t idx = threadIdx.x; idx < (int64_t)a.npad * padk; idx += blockDim.x) {
         const int64_t nn = idx / padk, o = nn * a.kp + a.rows + (idx - nn * padk);
-        if (a.pack_mode == TC_BF16) {
+        if (tc_bf16(a.pack_mode)) {
             reinterpret_cast<__nv_bfloat16 *>(a.pack)[o] = __float2bfloat16_rn(0.f);
+            if (a.pack_mode == TC_BF16X2)
+                reinterpret_cast<__nv_bfloat16 *>(a.pack)[(int64_t)a.npad * a.kp + o] =
+                    __float2bfloat16_rn(0.f);
         } else {
             reinterpret_cast<float *>(a.pack)[o] = 0.f;
             if (a.pack_mode == TC_TF32X3)

@@ -25,7 +25,10 @@
 //    of taking turns); the packed factor stacks its TF32 high part over its
 //    TF32 remainder, so one N = 2 NPAD MMA gives A*B_hi and A*B_lo side by
 //    side in TMEM and a second (N = NPAD) adds A_lo*B_hi.  BF16: A and B in
-//    BF16, kind::f16.
+//    BF16, kind::f16.  BF16X2: A in BF16, the factor split into a BF16 high
+//    part and the BF16 rounding of its remainder, stacked as for TF32X3, so
+//    one N = 2 NPAD MMA per k step gives A*B_hi and A*B_lo side by side: the
+//    factor enters with ~2^-17 relative error, A with its one BF16 rounding.
 //  * Every wait is bounded by a global-timer deadline; on expiry the CTA
 //    raises the timeout bit of the status word, drains, frees TMEM and exits.
 #include <cuda.h>
@@ -151,7 +154,7 @@ __host__ __device__ constexpr uint32_t idesc(uint32_t fmt, int M, int N)
 template <int MODE>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc)
 {
-    if constexpr (MODE == TC_BF16) {
+    if constexpr (MODE == TC_BF16 || MODE == TC_BF16X2) {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
@@ -297,16 +300,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                const TcArgs p)
 {
     constexpr bool X3 = MODE == TC_TF32X3;
+    constexpr bool BF = MODE == TC_BF16 || MODE == TC_BF16X2;   // A and B in BF16
+    constexpr bool PAIR = X3 || MODE == TC_BF16X2;             // B = [B_hi; B_lo]
     // TF32X3 with NPAD <= 64: warps 2-5 split while warps 6-9 accumulate.
     // Wider factors keep all eight warps on both jobs (an accumulating thread
     // could not hold 2 x 128 columns).
     constexpr bool SR = X3 && NPAD <= 64;
     constexpr int SPLIT_T = SR ? kSplit : kEpi;   // threads that split
-    constexpr int NB = X3 ? 2 * NPAD : NPAD;                  // rows of the packed factor tile
+    constexpr int NB = PAIR ? 2 * NPAD : NPAD;                // rows of the packed factor tile
     constexpr uint32_t B_BYTES = NB * 128;
     constexpr uint32_t STAGE_BYTES = kABytes + B_BYTES;
     constexpr uint32_t TX_BYTES = kABytes + B_BYTES;
-    constexpr int KSTEP_ELEMS = MODE == TC_BF16 ? 64 : 32;   // elements per 128-byte row
+    constexpr int KSTEP_ELEMS = BF ? 64 : 32;                 // elements per 128-byte row
     constexpr int KMMA = 4;                                   // MMAs of 32 bytes per stage
     constexpr uint32_t BUF_COLS = NB <= 32 ? 32 : (NB <= 64 ? 64 : (NB <= 128 ? 128 : 256));
     // MMA issuers and accumulator buffers: each issuer owns every NISS-th
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     static_assert(TMEM_USED <= 512, "tensor memory columns");
     constexpr uint32_t TMEM_COLS = TMEM_USED <= 32 ? 32 : TMEM_USED <= 64 ? 64 :
                                    TMEM_USED <= 128 ? 128 : TMEM_USED <= 256 ? 256 : 512;
-    constexpr uint32_t ID_B = idesc(MODE == TC_BF16 ? 1u : 2u, 128, NB);     // A x packed tile
+    constexpr uint32_t ID_B = idesc(BF ? 1u : 2u, 128, NB);                  // A x packed tile
     constexpr uint32_t ID_HI = idesc(2u, 128, NPAD);                         // A_lo x B_hi
     // Issuer q owns the k blocks of every NISS-th window of DRAIN consecutive
     // blocks of this CTA (windows are cut at row-tile boundaries into
@@ -632,7 +637,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             tc_fence_after();
             ld_add(tmem + b * BUF_COLS + lane_base);
-            if constexpr (X3)
+            if constexpr (PAIR)   // A B_lo (and for X3 A_lo B_hi) beside A B_hi
                 ld_add(tmem + b * BUF_COLS + NPAD + lane_base);
             tc_fence_before();
             mbar_arrive(&acc_empty[b]);
@@ -750,11 +755,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ---- factor packing: X (K x r, row-major) -> B (NPAD x Kp, K contiguous) --
 // mode TF32: raw FP32; TF32X3: 2 NPAD rows, the TF32 high part stacked over
-// the TF32 remainder; BF16: round to nearest BF16.  Rows r..NPAD-1 (of each
-// part) and columns K..Kp-1 are zero.
+// the TF32 remainder; BF16: round to nearest BF16; BF16X2: 2 NPAD rows, the
+// nearest BF16 value over the nearest BF16 value of the remainder.  Rows
+// r..NPAD-1 (of each part) and columns K..Kp-1 are zero.
 template <int MODE>
 __global__ void k_pack_factor(const float *__restrict__ X, int64_t K, int r, int npad, int64_t kp,
-                              void *__restrict__ Bhi, float *__restrict__ Blo)
+                              void *__restrict__ Bhi, void *__restrict__ Blo)
 {
     // TF32X3: Bhi rows [0, npad) hold the nearest TF32 value, Blo (= rows
     // [npad, 2 npad) of the same buffer) the nearest TF32 value of the rest
@@ -775,10 +781,15 @@ __global__ void k_pack_factor(const float *__restrict__ X, int64_t K, int r, int
         const float v = t[threadIdx.x][i];
         if constexpr (MODE == TC_BF16) {
             reinterpret_cast<__nv_bfloat16 *>(Bhi)[(int64_t)n * kp + k] = __float2bfloat16_rn(v);
+        } else if constexpr (MODE == TC_BF16X2) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            reinterpret_cast<__nv_bfloat16 *>(Bhi)[(int64_t)n * kp + k] = hi;
+            reinterpret_cast<__nv_bfloat16 *>(Blo)[(int64_t)n * kp + k] =
+                __float2bfloat16_rn(v - __bfloat162float(hi));
         } else if constexpr (MODE == TC_TF32X3) {
             const float hi = rn_tf32(v);
             reinterpret_cast<float *>(Bhi)[(int64_t)n * kp + k] = hi;
-            Blo[(int64_t)n * kp + k] = rn_tf32(v - hi);
+            reinterpret_cast<float *>(Blo)[(int64_t)n * kp + k] = rn_tf32(v - hi);
         } else {
             reinterpret_cast<float *>(Bhi)[(int64_t)n * kp + k] = v;
         }
@@ -826,7 +837,7 @@ struct TcCfg {
     // its shared-memory copy: only without the split warps (NPAD 128); with
     // them (NPAD <= 64) the ring is in tensor memory
     static constexpr int NLO_SM = MODE == TC_TF32X3 && NPAD > 64 ? NLO : 0;
-    static constexpr int NB = MODE == TC_TF32X3 ? 2 * NPAD : NPAD;
+    static constexpr int NB = MODE == TC_TF32X3 || MODE == TC_BF16X2 ? 2 * NPAD : NPAD;
     static constexpr int STAGE = kABytes + NB * 128;
     // as many stages as fit: A in flight from HBM is what the ring buys
     static constexpr int STG = 4 * 8 * NPAD * 4;                // epilogue staging bytes
@@ -887,13 +898,13 @@ int sm_count()
 
 int tc_npad(int r) { return r <= 16 ? 16 : r <= 32 ? 32 : r <= 64 ? 64 : 128; }
 
-int64_t tc_kpad(int64_t K, int mode) { return mode == TC_BF16 ? (K + 7) / 8 * 8 : (K + 3) / 4 * 4; }
+int64_t tc_kpad(int64_t K, int mode) { return tc_bf16(mode) ? (K + 7) / 8 * 8 : (K + 3) / 4 * 4; }
 
 size_t tc_pack_bytes(int64_t K, int r, int mode)
 {
     const int64_t kp = tc_kpad(K, mode);
-    const size_t e = mode == TC_BF16 ? 2 : 4;
-    return (size_t)tc_npad(r) * kp * e * (mode == TC_TF32X3 ? 2 : 1) + 256;
+    const size_t e = tc_bf16(mode) ? 2 : 4;
+    return (size_t)tc_npad(r) * kp * e * (tc_pair(mode) ? 2 : 1) + 256;
 }
 
 cudaError_t launch_tc_pack(const float *X, int64_t K, int r, int mode, void *pack, cudaStream_t s)
@@ -901,12 +912,14 @@ cudaError_t launch_tc_pack(const float *X, int64_t K, int r, int mode, void *pac
     ProfScope prof_(KC_OTHER, s);
     const int npad = tc_npad(r);
     const int64_t kp = tc_kpad(K, mode);
-    const size_t hb = (size_t)npad * kp * (mode == TC_BF16 ? 2 : 4);
-    float *lo = reinterpret_cast<float *>(reinterpret_cast<char *>(pack) + hb);   // rows npad..
+    const size_t hb = (size_t)npad * kp * (tc_bf16(mode) ? 2 : 4);
+    void *lo = reinterpret_cast<char *>(pack) + hb;   // rows npad.. of the pair modes
     dim3 grid((unsigned)((kp + 31) / 32), (unsigned)((npad + 31) / 32));
     dim3 blk(32, 8);
     if (mode == TC_BF16)
         k_pack_factor<TC_BF16><<<grid, blk, 0, s>>>(X, K, r, npad, kp, pack, nullptr);
+    else if (mode == TC_BF16X2)
+        k_pack_factor<TC_BF16X2><<<grid, blk, 0, s>>>(X, K, r, npad, kp, pack, lo);
     else if (mode == TC_TF32X3)
         k_pack_factor<TC_TF32X3><<<grid, blk, 0, s>>>(X, K, r, npad, kp, pack, lo);
     else
@@ -917,14 +930,14 @@ cudaError_t launch_tc_pack(const float *X, int64_t K, int r, int mode, void *pac
 
 bool tc_supported(int64_t lda, int mode, const void *A)
 {
-    const int64_t align = mode == TC_BF16 ? 8 : 4;   // 16-byte row pitch
+    const int64_t align = tc_bf16(mode) ? 8 : 4;   // 16-byte row pitch
     return (lda % align) == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0 && encode_fn();
 }
 
 TcPlan tc_plan(int64_t M, int64_t K, int r, int mode, int max_grid)
 {
     TcPlan pl;
-    const int kstep = mode == TC_BF16 ? 64 : 32;
+    const int kstep = tc_bf16(mode) ? 64 : 32;
     pl.kblocks = (int)((K + kstep - 1) / kstep);
     pl.tiles = (int)((M + 127) / 128);
     pl.iters = (int64_t)pl.tiles * pl.kblocks;
@@ -952,10 +965,10 @@ cudaError_t launch_tc_cross(const void *A, int64_t M, int64_t K, int64_t lda, in
     if (M <= 0)
         return cudaSuccess;
     const int npad = tc_npad(r);
-    const bool bf = mode == TC_BF16;
+    const bool bf = tc_bf16(mode);
     const int64_t kp = tc_kpad(K, mode);
     const size_t es = bf ? 2 : 4;
-    const uint32_t nb = mode == TC_TF32X3 ? 2 * npad : npad;   // packed rows ([hi; lo] for X3)
+    const uint32_t nb = tc_pair(mode) ? 2 * npad : npad;   // packed rows ([hi; lo] for the pairs)
     CUtensorMap ma, mb;
     const uint32_t box_k = bf ? 64 : 32;
     if (!make_map(&ma, A, bf, (uint64_t)K, (uint64_t)M, (uint64_t)lda * es, box_k, 128) ||
@@ -972,6 +985,8 @@ cudaError_t launch_tc_cross(const void *A, int64_t M, int64_t K, int64_t lda, in
     p.status = status;
     if (mode == TC_BF16)
         return launch_npad<TC_BF16>(npad, ma, mb, p, s);
+    if (mode == TC_BF16X2)
+        return launch_npad<TC_BF16X2>(npad, ma, mb, p, s);
     if (mode == TC_TF32X3)
         return launch_npad<TC_TF32X3>(npad, ma, mb, p, s);
     return launch_npad<TC_TF32>(npad, ma, mb, p, s);

@@ -168,7 +168,10 @@ cudaError_t launch_transpose_f32(const float *A, int64_t rows, int64_t cols, int
                                  float *out, cudaStream_t s);
 
 // ---- tensor-core cross term (tcgen05) ---------------------------------------
-enum TcMode { TC_TF32 = 0, TC_TF32X3 = 1, TC_BF16 = 2 };
+enum TcMode { TC_TF32 = 0, TC_TF32X3 = 1, TC_BF16 = 2, TC_BF16X2 = 3 };
+// operands in BF16 (A and the packed factor); factor packed as [hi; lo]
+__host__ __device__ constexpr bool tc_bf16(int mode) { return mode == TC_BF16 || mode == TC_BF16X2; }
+__host__ __device__ constexpr bool tc_pair(int mode) { return mode == TC_TF32X3 || mode == TC_BF16X2; }
 struct TcArgs {
     int64_t M;
     int r;

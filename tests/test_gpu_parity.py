@@ -290,10 +290,12 @@ def test_gram(h, rows, r):
 
 
 # element-wise bounds of one product term, relative to |x_a x_b|: round to
-# nearest TF32 / BF16 moves each operand by at most 2^-11 / 2^-9 of itself; the
-# hi + lo BF16 split represents x to within 2^-18 and drops lo lo
-GRAM_TOL = {"fp32": 2e-6, "tf32": 2.0 ** -10 + 2e-6, "bf16": 2.0 ** -8 + 2e-6,
-            "bf16x2": 3 * 2.0 ** -18 + 2e-6}
+# nearest TF32 (11 significant bits) / BF16 (8) moves each operand by at most
+# 2^-11 / 2^-8 of itself, so a product by 2^-10 / 2^-7; the hi + lo BF16
+# split represents x to within 2^-8 |x - hi| <= 2^-16 |x| and drops lo lo
+# (|lo| <= 2^-8 |x|), so a product moves by at most 3 * 2^-16
+GRAM_TOL = {"fp32": 2e-6, "tf32": 2.0 ** -10 + 2e-6, "bf16": 2.0 ** -7 + 2e-6,
+            "bf16x2": 3 * 2.0 ** -16 + 2e-6}
 
 
 @pytest.mark.parametrize("prec", ["tf32", "bf16", "bf16x2"])

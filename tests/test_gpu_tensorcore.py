@@ -9,8 +9,11 @@ registers every k block, the small terms in columns of their own; measured
 1.2e-7 norm-wise at K = 10000) 2e-6; TF32 truncates both operands to a 10-bit
 mantissa, so each product is off by less than 2^-9 of itself: 2^-9 + 2e-6;
 BF16 with A already BF16 (the oracle sees the same A) and B rounded to
-nearest BF16 inside the kernel, each product off by at most 2^-9 of itself:
-2^-9 + 2e-6.  These are worst-case bounds, not fits.
+nearest BF16 inside the kernel (8 significant bits: off by at most 2^-8 of
+itself), each product off by at most 2^-8 of itself: 2^-8 + 2e-6; BF16X2
+with the same A and B split into hi = rn(B) and lo = rn(B - hi), so that
+|B - hi - lo| <= 2^-8 |B - hi| <= 2^-16 |B| (BF16 products are exact in the
+FP32 accumulator): 2^-16 + 2e-6.  These are worst-case bounds, not fits.
 """
 import numpy as np
 import pytest
@@ -65,20 +68,24 @@ def test_tc_cross_tf32(h, M, K, r):
     print(f"tc tf32 M={M} K={K} r={r}: rel {err:.3e} worst {worst:.3f} x bound")
 
 
-@pytest.mark.parametrize("M,K", [(129, 96), (1000, 3008), (4096, 10000)])
-@pytest.mark.parametrize("r", [16, 50, 128])
-def test_tc_cross_bf16(h, M, K, r):
+BF16_BOUND = {"bf16": 2.0 ** -8 + 2e-6, "bf16x2": 2.0 ** -16 + 2e-6}
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x2"])
+@pytest.mark.parametrize("M,K", [(1, 64), (129, 96), (1000, 3008), (300, 20000), (4096, 10000)])
+@pytest.mark.parametrize("r", [4, 16, 50, 128])
+def test_tc_cross_bf16(h, M, K, r, prec):
     g = WL.rng(M + K + r + 2)
     A = g.random((M, K)).astype(np.float32)
     B = g.random((K, r)).astype(np.float32)
     Ab = torch.tensor(A, device=dev()).to(torch.bfloat16)
-    # the oracle sees the BF16-rounded A; B is rounded inside the kernel
+    # the oracle sees the BF16-rounded A; B is rounded (split) inside the kernel
     Co = O.cross_dense(Ab.float().cpu().numpy().astype(np.float64), B.astype(np.float64))
-    Cg = P.nmf_cross(h, Ab, t32(B), prec="bf16")
+    Cg = P.nmf_cross(h, Ab, t32(B), prec=prec)
     h.sync()
     err = rel_err(to_np(Cg), Co)
-    worst = elementwise_ok(to_np(Cg), Co, Co, 2.0 ** -9 + 2e-6)
-    print(f"tc bf16 M={M} K={K} r={r}: rel {err:.3e} worst {worst:.3f} x bound")
+    worst = elementwise_ok(to_np(Cg), Co, Co, BF16_BOUND[prec])
+    print(f"tc {prec} M={M} K={K} r={r}: rel {err:.3e} worst {worst:.3f} x bound")
 
 
 def test_tc_cross_unaligned_falls_back(h):
@@ -112,7 +119,7 @@ def test_tc_and_simt_solves_agree(h):
     assert np.abs(out[0][2] - out[1][2]).max() / out[1][2].max() < 1e-4
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "bf16x2"])
 def test_reduced_precision_solves_track_fp32(h, prec):
     """Solve with TF32 / BF16 cross terms (FP32 accumulation; Grams and NNLS
     in FP32) against the FP32 solve from the same start, on the non-chaotic
