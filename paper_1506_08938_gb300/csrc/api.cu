@@ -618,6 +618,7 @@ struct HalfStep {
     int64_t lda_tc;
     TcPlan plan;        // stream-K plan of the tensor-core cross term
     void *pack;         // packed other factor
+    int lanes;          // NQP layout of this half-step (lanes per row)
 };
 
 struct Loop {
@@ -733,7 +734,7 @@ nmf_status enqueue_half(nmf_handle h, Loop &L, HalfStep &s, float *G, HalfStep &
     a.cd_steps = L.nn.cd_steps;
     a.maxstop_mode = L.nn.maxstop_mode;
     a.maxstop = 0.f;
-    a.lanes = L.nn.lanes;
+    a.lanes = s.lanes;
     a.grad_refresh = L.nn.grad_refresh;
     a.iter_total = h->ctr;
     a.status = h->status;
@@ -1016,6 +1017,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     // on 50000 and 100000 rows).  The layout is fixed for the whole solve.
     if (L.nn.lanes == 0 && r > 64 && (m < n ? m : n) >= 32768)
         L.nn.lanes = 8;
+    const int lanes_w = L.nn.lanes, lanes_h = L.nn.lanes;
 
     // ---- workspace layout
     L.gS_w = gram_splits(m);
@@ -1028,8 +1030,9 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     // the NQP kernel prepares the factor it solved when its layout carries
     // the epilogue (RP <= 64): one Gram partial per CTA
     {
-        int lg = 0, lj = 0;
-        L.fuse_prep = nnls_layout(r, L.nn.lanes, &lg, &lj) && lg * lj <= 64;
+        int lg = 0, lj = 0, lg2 = 0, lj2 = 0;
+        L.fuse_prep = nnls_layout(r, lanes_w, &lg, &lj) && lg * lj <= 64 &&
+                      nnls_layout(r, lanes_h, &lg2, &lj2) && lg2 * lj2 <= 64;
         if (L.fuse_prep)
             gS = gS > kPrepMaxSlices ? gS : kPrepMaxSlices;
         L.Pg_slices = kPrepMaxSlices;
@@ -1185,6 +1188,8 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
         hh.K = m;
         hh.nsplit = sh;
     }
+    hw.lanes = lanes_w;
+    hh.lanes = lanes_h;
     hw.ms_thr = h->smax + 0;
     hh.ms_thr = h->smax + 1;
     hw.ms_out = h->smax + 2;
@@ -1218,11 +1223,12 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
         // the NQP launches' grids are the partial counts of the finishing launches
         NnlsArgs q{};
         q.r = r;
-        q.lanes = L.nn.lanes;
+        q.lanes = lanes_w;
         q.gram_P = L.Pg;
         q.gram_smax = L.Pg_slices;
         q.rows = m;
         L.S_w = nnls_grid_query(q);
+        q.lanes = lanes_h;
         q.rows = n;
         L.S_h = nnls_grid_query(q);
         if (L.S_w < 1 || L.S_h < 1)
@@ -1267,7 +1273,8 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     long long per_iter_launches = 0;
-    CK(prepare_nnls(r, L.nn.lanes));
+    CK(prepare_nnls(r, lanes_w));
+    CK(prepare_nnls(r, lanes_h));
     if (o.use_graph && o.outer_iters > 0) {
         if (!h->cap)
             CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));

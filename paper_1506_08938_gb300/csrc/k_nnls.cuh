@@ -14,13 +14,16 @@
 // coordinates: chunk c covers (c*G + li)*CW ... +CW-1, so that the G lanes of
 // a group read one contiguous run of any Qt row (no shared-memory bank
 // conflicts).  RP = G*J >= r.  The iterate y of each group lives in shared
-// memory in coordinate order: a coordinate step changes one entry, which its
-// owner lane rewrites, and every lane reloads its chunks at the next step.
+// memory in coordinate order, where the matrix-vector products read it;
+// during the coordinate steps each lane keeps its J entries in registers (a
+// step changes one entry, which only its owner lane reads) and writes them
+// back after the last step.
 // Qt, zero-padded to RP x RP, is loaded once per CTA; it is symmetric, so the
 // column Qt[:, p] a coordinate step needs is read as the contiguous row p.
 //
 // Per coordinate step a lane evaluates the gains of its J coordinates, the
-// group takes the maximum key with log2(G) xor-shuffles, and a ballot names
+// group takes the maximum key with log2(G) xor-shuffles (one warp-wide
+// reduction when G = 32), and a ballot names
 // the lowest lane holding it; within a lane the lower index wins, so exact
 // ties go to the lowest coordinate, as in the oracle.
 //
@@ -110,12 +113,18 @@ __device__ __forceinline__ float group_sum(float v)
 template <int G>
 __device__ __forceinline__ unsigned group_max(unsigned v)
 {
+    if constexpr (G == 32) {
+        // one row per warp: a single warp-wide reduction instead of five
+        // shuffle-and-max rounds (the maximum of integers: the same value)
+        return __reduce_max_sync(kFull, v);
+    } else {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-        unsigned w = __shfl_xor_sync(kFull, v, o);
-        v = w > v ? w : v;
+        for (int o = G / 2; o > 0; o >>= 1) {
+            unsigned w = __shfl_xor_sync(kFull, v, o);
+            v = w > v ? w : v;
+        }
+        return v;
     }
-    return v;
 }
 
 // all G ballot bits of one group set
@@ -576,10 +585,14 @@ __device__ __forceinline__ uint2 nnls_rows(const NnlsArgs &a, const float *__res
             }
         }
 
-        // ---- greedy coordinate descent: T steps of the largest decrease
+        // ---- greedy coordinate descent: T steps of the largest decrease.
+        // A step changes one coordinate, owned by one lane, and only that
+        // lane reads it during the steps: the iterate stays in registers and
+        // goes back to shared memory after the last step.
+        float yc[J];
+        ld_lane<G, J>(ysg, li, yc);
         for (int t = 0; t < T; ++t) {
-            float y[J];
-            ld_lane<G, J>(ysg, li, y);
+            const float(&y)[J] = yc;
             unsigned key[J];
             int idx[J];
             float del[J];
@@ -616,9 +629,13 @@ __device__ __forceinline__ uint2 nnls_rows(const NnlsArgs &a, const float *__res
 #pragma unroll
             for (int j = 0; j < J; ++j)
                 g[j] = fmaf(col[j], dp, g[j]);
-            if (step && lane == src)
-                ysg[p] += dp;
+            const unsigned own = (step && lane == src) ? 1u << pj : 0u;
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+                yc[j] = ((own >> j) & 1u) ? yc[j] + dp : yc[j];
         }
+        st_lane<G, J>(ysg, li, yc);
+        __syncwarp();   // the products below read every group's iterate
 
         // ---- stop test (Alg. 3): accelerated condition, fast break, cap
         float y[J];
