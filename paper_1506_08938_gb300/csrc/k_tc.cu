@@ -132,6 +132,23 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// bulk copy shared -> global of `bytes` (a multiple of 16; both addresses
+// 16-byte aligned), tracked by this thread's bulk groups
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
+                     reinterpret_cast<uint64_t>(gdst)),
+                 "r"(su32(ssrc)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// this thread's bulk copies have read their shared-memory source
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// this thread's bulk copies have completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // shared-memory matrix descriptor: K-major rows of 128 bytes, 128B swizzle,
 // 8-row core groups 1024 bytes apart (tiles are 1024-byte aligned)
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
@@ -306,6 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Wider factors keep all eight warps on both jobs (an accumulating thread
     // could not hold 2 x 128 columns).
     constexpr bool SR = X3 && NPAD <= 64;
+    constexpr bool BULK = NPAD <= 64;   // partial tiles leave by bulk copy (see the epilogue)
     constexpr int SPLIT_T = SR ? kSplit : kEpi;   // threads that split
     constexpr int NB = PAIR ? 2 * NPAD : NPAD;                // rows of the packed factor tile
     constexpr uint32_t B_BYTES = NB * 128;
@@ -350,9 +368,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     // the shared-memory low-part ring (NPAD 128 only; SR keeps it in TMEM)
     constexpr int NLO_SM = SR ? 0 : NLO;
     auto LO = [&](int j) { return smem + STAGES * STAGE_BYTES + j * kABytes; };
-    // epilogue staging: 8 rows x NPAD floats per TMEM lane quadrant
+    // epilogue staging: 32 (BULK) or 8 rows x NPAD floats per TMEM lane quadrant
+    constexpr int STG_ROWS = BULK ? 32 : 8;
     float *stg_all = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + NLO_SM * kABytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stg_all + 4 * 8 * NPAD);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stg_all + 4 * STG_ROWS * NPAD);
     uint64_t *full = bars, *empty = bars + NF;
     uint64_t *lo_full = empty + STAGES, *lo_empty = lo_full + NLF;
     uint64_t *acc_full = lo_empty + (NLO > 0 ? NLO : 1), *acc_empty = acc_full + NACC;
@@ -695,17 +714,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int c_last = owner_of(last_it, p.iters, p.grid);
             const int slice = (int)blockIdx.x - c_first;
             // The rows of this quadrant form one contiguous run of the slice
-            // (rows of r floats).  Groups of 8 rows go through shared memory
-            // and out with consecutive threads on consecutive floats: a row
-            // per thread straight to global memory would cost a separate
-            // memory transaction for every lane of every store.
+            // (rows of r floats).  NPAD <= 64: the quadrant stages its 32 rows
+            // whole in shared memory in that layout and one thread sends them
+            // with a bulk copy, so the accumulating warps go back to the next
+            // chunk at once (the stores used to hold the drain, and behind it
+            // the ring, for several microseconds a launch); wider factors go
+            // through in groups of 8 rows with consecutive threads on
+            // consecutive floats (a row per thread straight to global memory
+            // would cost a separate transaction for every lane of every store).
             const int r = p.r;
             const int64_t row0 = (int64_t)tile * 128 + quad * 32;
             const int64_t left = p.M - row0;
             const int nrow = left <= 0 ? 0 : (left < 32 ? (int)left : 32);
             constexpr int QT = SR ? 32 : 64;                  // threads of a quadrant
             const int qt = SR ? lane : half * 32 + lane;
-            float *stg = stg_all + quad * 8 * NPAD;
             auto qsync = [&]() {
                 if constexpr (SR)
                     __syncwarp();
@@ -713,20 +735,43 @@ __global__ void __launch_bounds__(kThreads, 1)
                     asm volatile("bar.sync %0, 64;" ::"r"(1 + quad) : "memory");
             };
             float *dst = p.P + (int64_t)slice * p.M * r + row0 * r;
-            for (int g = 0; g < nrow; g += 8) {
-                const int nr = nrow - g < 8 ? nrow - g : 8;
-                if (lane >= g && lane < g + nr) {
-                    float *sr = stg + (lane - g) * r + half * HC;
+            if constexpr (BULK) {
+                float *stg = stg_all + quad * 32 * NPAD;
+                if (qt == 0)
+                    bulk_wait_read();   // the previous copy has read the buffer
+                qsync();
+                if (lane < nrow) {
+                    float *sr = stg + lane * r + half * HC;
 #pragma unroll
                     for (int j = 0; j < HC; ++j)
                         if (half * HC + j < r)
                             sr[j] = acc[j];
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 qsync();
-                float *d = dst + (int64_t)g * r;
-                for (int e = qt; e < nr * r; e += QT)
-                    d[e] = stg[e];
-                qsync();
+                const int n = nrow * r;
+                const int nb = (reinterpret_cast<uintptr_t>(dst) & 15u) == 0 ? (n & ~3) : 0;
+                if (qt == 0 && nb > 0)
+                    bulk_store(dst, stg, (uint32_t)nb * 4u);
+                for (int e = nb + qt; e < n; e += QT)
+                    dst[e] = stg[e];
+            } else {
+                float *stg = stg_all + quad * 8 * NPAD;
+                for (int g = 0; g < nrow; g += 8) {
+                    const int nr = nrow - g < 8 ? nrow - g : 8;
+                    if (lane >= g && lane < g + nr) {
+                        float *sr = stg + (lane - g) * r + half * HC;
+#pragma unroll
+                        for (int j = 0; j < HC; ++j)
+                            if (half * HC + j < r)
+                                sr[j] = acc[j];
+                    }
+                    qsync();
+                    float *d = dst + (int64_t)g * r;
+                    for (int e = qt; e < nr * r; e += QT)
+                        d[e] = stg[e];
+                    qsync();
+                }
             }
             // the first part of a tile clears the slices no CTA writes for it
             if (slice == 0) {
@@ -740,6 +785,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int j = 0; j < HC; ++j)
                 acc[j] = 0.f;
         }
+        // the bulk copies this thread issued complete before the CTA exits
+        if constexpr (BULK)
+            bulk_wait_all();
     }
     __syncthreads();
     if (threadIdx.x == 0 && *abort_flag && p.status)
@@ -840,8 +888,9 @@ struct TcCfg {
     static constexpr int NB = MODE == TC_TF32X3 || MODE == TC_BF16X2 ? 2 * NPAD : NPAD;
     static constexpr int STAGE = kABytes + NB * 128;
     // as many stages as fit: A in flight from HBM is what the ring buys
-    static constexpr int STG = 4 * 8 * NPAD * 4;                // epilogue staging bytes
-    static constexpr int ST0 = (220 * 1024 - NLO_SM * (int)kABytes - STG) / STAGE;
+    // epilogue staging bytes: 32 rows per TMEM lane quadrant (NPAD <= 64), else 8
+    static constexpr int STG = 4 * (NPAD <= 64 ? 32 : 8) * NPAD * 4;
+    static constexpr int ST0 = (225 * 1024 - NLO_SM * (int)kABytes - STG) / STAGE;
     static constexpr int STAGES = ST0 > 8 ? 8 : ST0;
     static constexpr int DRAIN = MODE == TC_TF32X3 ? 1 : 2;     // k blocks per chunk
     // + 1024 for the 1024-byte alignment of the tiles, + the barrier area
