@@ -1089,7 +1089,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     const size_t n_objp = L.direct_obj ? objective_direct_partials(m, n) : 0;
     Sizer z;
     z.add<double>(n_objp);
-    z.add<float>((size_t)gS * r * r);
+    z.add<float>((size_t)gS * prep_slice_floats(r));
     z.add<unsigned>(4);
     z.add<float>((size_t)r * r);
     z.add<float>((size_t)r * r);
@@ -1115,7 +1115,7 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
         L.V = (const float *)V->d.data;
         L.ldv = V->d.ld;
     }
-    L.Pg = a.take<float>((size_t)gS * r * r);
+    L.Pg = a.take<float>((size_t)gS * prep_slice_floats(r));
     L.ticket = a.take<unsigned>(4);
     L.Gw = a.take<float>((size_t)r * r);
     L.Gh = a.take<float>((size_t)r * r);

@@ -7,8 +7,8 @@
 // Two launches replace four (Gram partials, slice sum, rescale, packing):
 //   1. CTAs over row ranges of 32+ rows accumulate Gram partials in registers
 //      and write their columns of the packed factor;
-//   2. CTAs over 32-element column groups of G sum the partials - 16 warps
-//      over interleaved slices, then the warp sums in warp order: a fixed
+//   2. CTAs over 128-element column groups of G sum the partials - 32 warps
+//      over interleaved slices, 16-byte loads, then the warp sums in warp order: a fixed
 //      order, so the result is reproducible - and the last CTA to finish
 //      (ticket counter) rescales and clears the counter.
 // Both kernels issue their global loads in batches before using them: a
@@ -19,7 +19,7 @@ namespace nmfi {
 namespace {
 
 using namespace prep_detail;
-constexpr int kSumWarps = 16;      // warps of a reduction CTA
+constexpr int kSumWarps = 32;      // warps of a reduction CTA
 
 template <int NB>
 __global__ void __launch_bounds__(kThreads) k_factor_prep(const PrepArgs a)
@@ -37,41 +37,62 @@ __global__ void __launch_bounds__(kThreads) k_factor_prep(const PrepArgs a)
     gram_pack_rows<NB>(a, Xs, k0, k1, blockIdx.x);
 }
 
-constexpr int kPerWarp = (kMaxSlices + kSumWarps - 1) / kSumWarps;   // slices per warp at most
+constexpr int kBatch = 8;          // 16-byte loads a thread has in flight
 
-// G[e] = sum_s P[s][e] for groups of 32 consecutive e (group g on CTA
-// g mod gridDim.x), then (last CTA) Q, Qt, d
-__global__ void __launch_bounds__(kSumWarps * 32) k_prep_finish(const PrepArgs a, int S)
+// G[e] = sum_s P[s][e] for groups of 32 float4 columns (128 elements; group
+// g on CTA g mod gridDim.x): warp w adds the slices w, w + kSumWarps, ... in
+// order, kBatch loads issued before their adds, then the warps' sums are
+// added in warp order - a fixed order, so the result is reproducible - and
+// the last CTA to finish (ticket counter) forms Q, Qt, d
+__global__ void __launch_bounds__(kSumWarps * 32, 1) k_prep_finish(const PrepArgs a, int S)
 {
-    __shared__ float part[kSumWarps][33];
+    __shared__ float4 part[kSumWarps][32];
     __shared__ float sd[kMaxRank];
     __shared__ int last;
     pdl_trigger();
     pdl_wait();   // the partials are the previous kernel's output
-    const int r = a.r, n = r * r;
+    const int r = a.r, n = r * r, n4 = prep_slice_floats(r) / 4;
+    const float4 *P4 = reinterpret_cast<const float4 *>(a.P);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int eg = blockIdx.x; eg * 32 < n; eg += gridDim.x) {
-        const int e = eg * 32 + lane;
-        // this warp's slices w, w + kSumWarps, ... in order, every load
-        // issued before the first add
-        float v[kPerWarp];
+    for (int g = blockIdx.x; g * 32 < n4; g += gridDim.x) {
+        const int c = g * 32 + lane;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k0 = w; k0 < S; k0 += kBatch * kSumWarps) {
+            float4 v[kBatch];
 #pragma unroll
-        for (int u = 0; u < kPerWarp; ++u) {
-            const int k = w + u * kSumWarps;
-            v[u] = (e < n && k < S) ? a.P[(int64_t)k * n + e] : 0.f;
+            for (int u = 0; u < kBatch; ++u) {
+                const int k = k0 + u * kSumWarps;
+                v[u] = (c < n4 && k < S) ? P4[(int64_t)k * n4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                acc.x += v[u].x;
+                acc.y += v[u].y;
+                acc.z += v[u].z;
+                acc.w += v[u].w;
+            }
         }
-        float acc = 0.f;
-#pragma unroll
-        for (int u = 0; u < kPerWarp; ++u)
-            acc += v[u];
         part[w][lane] = acc;
         __syncthreads();
-        if (w == 0 && e < n) {
-            float s = 0.f;
-#pragma unroll
-            for (int q = 0; q < kSumWarps; ++q)
-                s += part[q][lane];
-            a.G[e] = s;
+        if (w == 0 && c < n4) {
+            float4 t = part[0][lane];
+#pragma unroll 4
+            for (int q = 1; q < kSumWarps; ++q) {
+                const float4 u = part[q][lane];
+                t.x += u.x;
+                t.y += u.y;
+                t.z += u.z;
+                t.w += u.w;
+            }
+            const int e = 4 * c;   // the padding floats past n are dropped
+            if (e < n)
+                a.G[e] = t.x;
+            if (e + 1 < n)
+                a.G[e + 1] = t.y;
+            if (e + 2 < n)
+                a.G[e + 2] = t.z;
+            if (e + 3 < n)
+                a.G[e + 3] = t.w;
         }
         __syncthreads();   // part is rewritten by the next group
     }
@@ -110,6 +131,9 @@ __global__ void __launch_bounds__(kSumWarps * 32) k_prep_finish(const PrepArgs a
     if (threadIdx.x == 0)
         *a.ticket = 0u;   // ready for the next launch (graph replays included)
 }
+
+// groups of 32 float4 columns (128 elements) of one partial slice
+int finish_groups(int r) { return (prep_slice_floats(r) / 4 + 31) / 32; }
 
 }  // namespace
 
@@ -150,8 +174,7 @@ cudaError_t launch_factor_prep(const PrepArgs &a0, cudaStream_t s)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    const int n = a.r * a.r;
-    e = pdl_launch(k_prep_finish, dim3((n + 31) / 32), dim3(kSumWarps * 32), 0, s, a, S);
+    e = pdl_launch(k_prep_finish, dim3(finish_groups(a.r)), dim3(kSumWarps * 32), 0, s, a, S);
     count_launch();
     return e;
 }
@@ -161,7 +184,7 @@ cudaError_t launch_prep_finish_narrow(const PrepArgs &a, int S, int ctas, cudaSt
     ProfScope prof_(KC_GRAM, s);
     if (a.rows <= 0 || a.r < 1 || a.r > kMaxRank || !a.G || S < 1 || S > kMaxSlices || ctas < 1)
         return cudaErrorInvalidValue;
-    const int groups = (a.r * a.r + 31) / 32;
+    const int groups = finish_groups(a.r);
     k_prep_finish<<<ctas < groups ? ctas : groups, kSumWarps * 32, 0, s>>>(a, S);
     count_launch();
     return cudaGetLastError();
@@ -172,8 +195,7 @@ cudaError_t launch_prep_finish(const PrepArgs &a, int S, cudaStream_t s)
     ProfScope prof_(KC_GRAM, s);
     if (a.rows <= 0 || a.r < 1 || a.r > kMaxRank || !a.G || S < 1 || S > kMaxSlices)
         return cudaErrorInvalidValue;
-    const int n = a.r * a.r;
-    cudaError_t e = pdl_launch(k_prep_finish, dim3((n + 31) / 32), dim3(kSumWarps * 32), 0, s, a, S);
+    cudaError_t e = pdl_launch(k_prep_finish, dim3(finish_groups(a.r)), dim3(kSumWarps * 32), 0, s, a, S);
     count_launch();
     return e;
 }

@@ -19,7 +19,8 @@ __device__ __forceinline__ float rn_tf32(float v)
 }
 
 // NB >= r columns: the Gram partial of rows [k0, k1) of a.X into slice
-// `slice` of a.P (r x r) and, if a.pack_mode >= 0, those rows' columns of the
+// `slice` of a.P (r x r, prep_slice_floats(r) floats per slice) and, if
+// a.pack_mode >= 0, those rows' columns of the
 // packed operand.  Xs: kRowsBlock x (NB + 1) floats of shared memory.  Every
 // thread of the (kThreads-thread) CTA calls it; it synchronises the CTA.
 template <int NB>
@@ -94,7 +95,7 @@ __device__ __forceinline__ void gram_pack_rows(const PrepArgs &a, float (*Xs)[NB
             }
         }
     }
-    float *Ps = a.P + slice * r * r;
+    float *Ps = a.P + slice * prep_slice_floats(r);
 #pragma unroll
     for (int i = 0; i < T; ++i)
 #pragma unroll

@@ -125,7 +125,7 @@ struct PrepArgs {
     int64_t rows;
     int r;
     float beta;             // L2 weight of the next half-step
-    float *P;               // partial Gram slices (prep_slices(rows) x r x r)
+    float *P;               // partial Gram slices, prep_slice_floats(r) apart (r x r each)
     unsigned *ticket;       // zero before the first launch; left zero
     float *G, *Q;           // optional: X^T X and X^T X + beta I
     float *Qt, *d;          // rescaled Q and its scale
@@ -138,11 +138,14 @@ struct PrepArgs {
                             // (the NQP kernel's split); 0: 32-row chunks
 };
 constexpr int kPrepMaxSlices = 512;   // Gram partial slices the finishing kernel sums at most
+// floats from one Gram partial slice to the next: r x r rounded up to a
+// multiple of 4, so that every slice starts on a 16-byte boundary
+__host__ __device__ constexpr int prep_slice_floats(int r) { return (r * r + 3) & ~3; }
 cudaError_t launch_factor_prep(const PrepArgs &a, cudaStream_t s);
 // the second launch alone, over S partial slices already in a.P (written by
 // the NQP kernel's epilogue)
 cudaError_t launch_prep_finish(const PrepArgs &a, int S, cudaStream_t s);
-// the same on `ctas` CTAs (each walks several 32-element groups), an ordinary
+// the same on `ctas` CTAs (each walks several 128-element groups), an ordinary
 // launch: for a side stream, beside the cross term
 cudaError_t launch_prep_finish_narrow(const PrepArgs &a, int S, int ctas, cudaStream_t s);
 int prep_slices(int64_t rows);
