@@ -1447,13 +1447,26 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
     }
     z.add<BatchInst>(count);
     z.add<int64_t>((size_t)8 * (count + 1));
+    z.add<unsigned long long>(8);
     nmf_status st = ensure_ws(h, z.off);
     if (st)
         return st;
     Arena a(h->ws, h->ws_cap);
+    // the device list in decreasing cross-term cost m n r (ties by position):
+    // with CTAs taking items in order, the largest instances start first;
+    // results do not depend on the order
+    std::vector<int> ord(count);
+    for (int i = 0; i < count; ++i)
+        ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+        return (double)inst[x].m * inst[x].n * inst[x].r > (double)inst[y].m * inst[y].n * inst[y].r;
+    });
+    std::vector<nmf_instance> pinst(count);
+    for (int j = 0; j < count; ++j)
+        pinst[j] = inst[ord[j]];
     std::vector<BatchInst> hb(count);
     for (int i = 0; i < count; ++i) {
-        const nmf_instance &b = inst[i];
+        const nmf_instance &b = pinst[i];
         BatchInst &q = hb[i];
         q.m = b.m;
         q.n = b.n;
@@ -1475,6 +1488,7 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
     }
     BatchInst *dinst = a.take<BatchInst>(count);
     int64_t *doff = a.take<int64_t>((size_t)8 * (count + 1));
+    unsigned long long *dwork = a.take<unsigned long long>(8);
     cudaStream_t s = h->stream;
     CK(cudaMemcpyAsync(dinst, hb.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, s));
 
@@ -1494,11 +1508,15 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
     ba.barrier_ns = fault_armed("barrier") ? 0ull : 2000000000ull;
     CK(cudaMemsetAsync(h->ctr + 1, 0, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(h->idev + 2, 0, 2 * sizeof(int), s));
+    CK(cudaMemsetAsync(dwork, 0, 8 * sizeof(unsigned long long), s));
+    // the launches over all instances take items from the counters; the
+    // one-instance launches of the loop mode keep the fixed stride
+    ba.work = mode == 1 ? nullptr : dwork;
 
     std::vector<int64_t> hoff;
     auto set_rows = [&](int rows) -> nmf_status {
         ba.nnls_rows = rows;
-        batch_offsets(hoff, inst, count, rows);
+        batch_offsets(hoff, pinst.data(), count, rows);
         CK(cudaMemcpyAsync(doff, hoff.data(), sizeof(int64_t) * hoff.size(),
                            cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));   // hoff is reused

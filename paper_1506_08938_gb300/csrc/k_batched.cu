@@ -8,8 +8,12 @@
 //   4 Gram partials of W       5 sum + L2 + rescale -> Qt_H, d_H
 //   6 cross C_H = V^T W        7 NNLS of every row of Ht
 // Each phase is a flat list of work items over all instances (row chunks,
-// row tiles, instances); a CTA takes items i, i + grid, ... and maps an item
-// to its instance by binary search over per-phase prefix sums.
+// row tiles, instances); a CTA maps an item to its instance by binary search
+// over per-phase prefix sums.  Item costs differ by two orders of magnitude
+// (K from 100 to 4000, r from 8 to 64), so CTAs take the next item from a
+// per-phase counter as they finish one, and the instances are ordered by
+// decreasing cost: the large items start first.  An item's result does not
+// depend on the CTA that computes it.
 //
 // Persistent mode: one cooperative launch runs all eight phases with grid
 // barriers in between (every CTA is resident: the grid is the occupancy
@@ -178,17 +182,22 @@ __device__ void rescale_item(const float *P, int nparts, int r, float beta, floa
 
 // cross term rows [m0, m0 + kCrossRows) of C = A B (A M x K row-major, B K x r,
 // r <= NB).  Thread (ty, tx) owns rows ty*TM .. ty*TM+TM-1 and columns
-// tx*4 .. tx*4+3; per k a 128-bit load of B and TM loads of A feed 4 TM FMAs.
-// The next 32-wide k tile is loaded into registers while this one is used.
+// tx*4 .. tx*4+3.  The A tile sits in shared memory transposed (k-major), so
+// a thread's TM rows at one k are contiguous: per k one vector load of A, one
+// 128-bit load of B and 4 TM FMAs (the row-major tile took TM scalar loads).
+// Each output adds its k terms in increasing k, one FMA each.  The next
+// 32-wide k tile is loaded into registers while this one is used.
 template <int NB>
 __device__ void cross_item(const float *A, int64_t M, int64_t K, const float *B, int r,
                            int64_t m0, float *C, float *sm)
 {
     constexpr int BM = kCrossRows, BK = 32, TX = NB / 4, TY = kT / TX, TM = BM / TY;
-    constexpr int LDA = BK + 1;
+    constexpr int LDT = BM + 4;             // floats per k row of the transposed A tile
     constexpr int AL = BM * BK / kT, BL = (BK * NB + kT - 1) / kT;   // loads per thread
-    float *As = sm;                         // BM x LDA
-    float *Bs = sm + BM * LDA;              // BK x NB (16-byte aligned: BM * LDA % 4 == 0)
+    static_assert(BK * LDT <= BM * (BK + 1) && TM <= 8 && (TM & (TM - 1)) == 0,
+                  "tile layout of the cross phase");
+    float *As = sm;                         // BK x LDT (A^T of the tile)
+    float *Bs = sm + BK * LDT;              // BK x NB (16-byte aligned: BK * LDT % 4 == 0)
     const int tid = threadIdx.x, ty = tid / TX, tx = tid - ty * TX;
     float acc[TM][4];
 #pragma unroll
@@ -217,7 +226,7 @@ __device__ void cross_item(const float *A, int64_t M, int64_t K, const float *B,
 #pragma unroll
         for (int q = 0; q < AL; ++q) {
             const int idx = tid + kT * q, mm = idx / BK, kk = idx - mm * BK;
-            As[mm * LDA + kk] = ra[q];
+            As[kk * LDT + mm] = ra[q];
         }
 #pragma unroll
         for (int q = 0; q < BL; ++q) {
@@ -231,13 +240,26 @@ __device__ void cross_item(const float *A, int64_t M, int64_t K, const float *B,
 #pragma unroll 8
         for (int kk = 0; kk < BK; ++kk) {
             const float4 b = *reinterpret_cast<const float4 *>(Bs + kk * NB + tx * 4);
+            const float *ap = As + kk * LDT + ty * TM;
+            float a[TM];
+            if constexpr (TM >= 4) {
+#pragma unroll
+                for (int i = 0; i < TM; i += 4) {
+                    const float4 t = *reinterpret_cast<const float4 *>(ap + i);
+                    a[i] = t.x; a[i + 1] = t.y; a[i + 2] = t.z; a[i + 3] = t.w;
+                }
+            } else if constexpr (TM == 2) {
+                const float2 t = *reinterpret_cast<const float2 *>(ap);
+                a[0] = t.x; a[1] = t.y;
+            } else {
+                a[0] = ap[0];
+            }
 #pragma unroll
             for (int i = 0; i < TM; ++i) {
-                const float a = As[(ty * TM + i) * LDA + kk];
-                acc[i][0] = fmaf(a, b.x, acc[i][0]);
-                acc[i][1] = fmaf(a, b.y, acc[i][1]);
-                acc[i][2] = fmaf(a, b.z, acc[i][2]);
-                acc[i][3] = fmaf(a, b.w, acc[i][3]);
+                acc[i][0] = fmaf(a[i], b.x, acc[i][0]);
+                acc[i][1] = fmaf(a[i], b.y, acc[i][1]);
+                acc[i][2] = fmaf(a[i], b.z, acc[i][2]);
+                acc[i][3] = fmaf(a[i], b.w, acc[i][3]);
             }
         }
     }
@@ -303,7 +325,18 @@ __device__ void run_phase(const BatchArgs &a, int phase, int64_t item_begin, int
     const BatchInst *I = a.inst;
     const int64_t *off = a.item_off + (int64_t)phase * (a.count + 1);
     const bool w_update = phase < 4;
-    for (int64_t item = item_begin; item < item_end; item += stride) {
+    __shared__ unsigned long long taken;
+    int64_t item = item_begin;
+    for (;;) {
+        if (a.work) {
+            if (threadIdx.x == 0)
+                taken = atomicAdd(a.work + phase, 1ull);
+            __syncthreads();
+            item = item_begin + (int64_t)taken;
+            __syncthreads();   // every thread has read it before it is replaced
+        }
+        if (item >= item_end)
+            break;
         const int i = find_inst(off, a.count, item);
         const int64_t local = item - off[i];
         const BatchInst &b = I[i];
@@ -351,6 +384,8 @@ __device__ void run_phase(const BatchArgs &a, int phase, int64_t item_begin, int
             break;
         }
         }
+        if (!a.work)
+            item += stride;
     }
 }
 
@@ -363,7 +398,11 @@ __global__ void __launch_bounds__(kT, 2) k_batched_iter(const BatchArgs a)
         const int64_t *off = a.item_off + (int64_t)phase * (a.count + 1);
         const int64_t lo = a.inst_begin >= 0 ? off[a.inst_begin] : 0;
         const int64_t hi = a.inst_begin >= 0 ? off[a.inst_begin + 1] : off[a.count];
-        run_phase(a, phase, lo + blockIdx.x, hi, gridDim.x, smem);
+        // the previous phase's counter is free (its phase ended behind a
+        // grid barrier or a kernel boundary): zero it for its next use
+        if (a.work && blockIdx.x == 0 && threadIdx.x == 0)
+            a.work[(phase + 7) & 7] = 0ull;
+        run_phase(a, phase, a.work ? lo : lo + blockIdx.x, hi, gridDim.x, smem);
         if (phase + 1 < a.phase_end) {
             if (!grid_barrier(a.bar_count, a.bar_gen, gridDim.x, a.status, a.barrier_ns))
                 return;

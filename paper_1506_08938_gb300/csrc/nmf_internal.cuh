@@ -227,6 +227,9 @@ struct BatchArgs {
     unsigned *status;
     unsigned *bar_count, *bar_gen;
     unsigned long long barrier_ns;   // grid-barrier deadline (kBarrierNs unless injected)
+    // per-phase item counters (8): CTAs take items in order from them instead
+    // of a fixed stride; null: the fixed stride (one-instance launches)
+    unsigned long long *work;
 };
 size_t batched_smem_bytes();
 int64_t batched_items(int phase, int64_t m, int64_t n, int r, int nnls_mult);
