@@ -330,6 +330,17 @@ nmf_status nmf_peak_fp32(double *tflops);
  * gathers hit L2.  Synchronises the device; allocates 32 MB at most. */
 nmf_status nmf_peak_l2_gather(int r, double *gbs);
 
+/* Dense BF16 throughput of this library's tcgen05.mma path in TFLOP/s
+ * (*tflops, host) on a contraction wide enough to be bound by the tensor
+ * pipe rather than HBM (r = 512): one CTA per SM issues, from shared-memory
+ * tiles, pairs of M = 128, N = 256, K = 16 MMAs into all 512 TMEM columns
+ * (the descriptors and issue path of nmf_cross), counted as 2 M N K each.
+ * The cross term itself is HBM-bound at r <= 128 (2 r / 4 flop per byte of
+ * FP32 V); this is the tensor-pipe roofline it sits under.  Synchronises the
+ * device; NMF_E_TIMEOUT if the bounded wait for the MMAs ran out (the
+ * handle's status word says so, the context stays usable). */
+nmf_status nmf_peak_tc_bf16(nmf_handle h, double *tflops);
+
 /* ---- projection onto a fixed basis ----------------------------------------- */
 
 /* E-step alone (Alg. 1 E-step, Alg. 2 first loop) against a fixed basis W

@@ -110,6 +110,7 @@ def _load():
     L.nmf_kkt.argtypes = [_P, _P, _P, C.c_int64, C.c_int, C.c_float, _P, _P]
     L.nmf_objective_direct.argtypes = [_P, C.POINTER(Dense), _P, _P, C.c_int, C.c_float,
                                        C.c_float, C.c_float, C.c_float, _P]
+    L.nmf_peak_tc_bf16.argtypes = [_P, C.POINTER(C.c_double)]
     L.nmf_solve.argtypes = [_P, C.POINTER(Matrix), C.POINTER(Matrix), C.c_int, _P, _P,
                             C.POINTER(SolveOpts), C.POINTER(Report)]
     L.nmf_solve_streamed.argtypes = [_P, C.POINTER(Dense), C.c_int, _P, _P,
@@ -136,6 +137,14 @@ def _load():
 
 
 KCLASS = {"gram": 0, "cross": 1, "spmm": 2, "rescale": 3, "nnls": 4, "objective": 5, "other": 6}
+
+
+def nmf_peak_tc_bf16(h: "Handle") -> float:
+    """Dense BF16 TFLOP/s of the library's tcgen05.mma path on an r = 512
+    contraction from shared memory (the tensor-pipe roofline)."""
+    t = C.c_double()
+    _check(lib().nmf_peak_tc_bf16(h.h, C.byref(t)), "nmf_peak_tc_bf16")
+    return t.value
 
 
 def nmf_peak_fp32() -> float:

@@ -1679,6 +1679,18 @@ NMF_API nmf_status nmf_peak_fp32(double *tflops)
     return NMF_OK;
 }
 
+NMF_API nmf_status nmf_peak_tc_bf16(nmf_handle h, double *tflops)
+{
+    if (!h || !tflops)
+        return NMF_E_ARG;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemset(h->status, 0, sizeof(unsigned)));
+    CK(measure_tc_peak(tflops, h->status));
+    unsigned st = 0;
+    CK(cudaMemcpy(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    return (st & kStTimeout) ? NMF_E_TIMEOUT : NMF_OK;
+}
+
 NMF_API nmf_status nmf_peak_l2_gather(int r, double *gbs)
 {
     if (!gbs)

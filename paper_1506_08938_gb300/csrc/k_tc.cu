@@ -879,6 +879,87 @@ bool make_map(CUtensorMap *m, const void *base, bool bf16, uint64_t inner, uint6
     return r == CUDA_SUCCESS;
 }
 
+// ---- tensor-pipe probe ------------------------------------------------------
+// The MMA path of the cross term on a contraction wide enough to be bound by
+// the tensor pipe instead of HBM (r = 512): one CTA per SM holds a 128 x 64
+// BF16 A tile and a 512 x 64 B tile in shared memory (128B-swizzled, as the
+// TMA would leave them) and one thread issues, per 16-wide k step, two
+// M = 128, N = 256 MMAs into the two halves of the 512 TMEM columns, cycling
+// over the tile's four k steps `iters` times; a commit to an mbarrier (bounded
+// wait) ends it.  The tiles hold BF16 values in [0.5, 1.5) from a hash of the
+// position.  A launch lasts about a millisecond, too short for the power cap
+// to lower the SM clock.
+constexpr int kPeakN = 256;
+constexpr uint32_t kPeakA = 128 * 128, kPeakB = 2 * kPeakN * 128;   // bytes
+constexpr size_t kPeakSmem = 120 * 1024;   // > half the SM's shared memory: one CTA per SM
+
+__global__ void __launch_bounds__(128, 1) k_tc_peak(int iters, unsigned *status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                ~uintptr_t(1023));
+    uint8_t *As = smem, *Bs = smem + kPeakA;
+    uint64_t *done = reinterpret_cast<uint64_t *>(Bs + kPeakB);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    for (uint32_t i = threadIdx.x; i < (kPeakA + kPeakB) / 4; i += blockDim.x) {
+        uint32_t hsh = (i + 1u) * 2654435761u;   // two BF16 values per word
+        hsh ^= hsh >> 15;
+        const float lo = 0.5f + (float)(hsh & 1023u) * (1.f / 1024.f);
+        const float hi = 0.5f + (float)((hsh >> 10) & 1023u) * (1.f / 1024.f);
+        const uint32_t w = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+                           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+        reinterpret_cast<uint32_t *>(smem)[i] = w;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(tmem_slot)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    if (threadIdx.x == 0) {
+        constexpr uint32_t ID = idesc(1u, 128, kPeakN);
+        const uint32_t a0 = su32(As), b0 = su32(Bs);
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                mma<TC_BF16>(tmem, sdesc(a0 + 32 * kk), sdesc(b0 + 32 * kk), ID, acc);
+                mma<TC_BF16>(tmem + kPeakN, sdesc(a0 + 32 * kk),
+                             sdesc(b0 + kPeakN * 128 + 32 * kk), ID, acc);
+            }
+        mma_commit(done);
+        const unsigned long long deadline = gtimer() + kDeadlineNs;
+        if (!mbar_wait(done, 0, deadline, abort_flag)) {
+            if (status)
+                atomicOr(status, kStTimeout);
+            mbar_wait_drain(done, 0, deadline + kDeadlineNs);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(512u)
+                     : "memory");
+    }
+}
+
 template <int MODE, int NPAD>
 struct TcCfg {
     static constexpr int NLO = MODE == TC_TF32X3 ? 3 : 0;       // low-part ring
@@ -1039,6 +1120,53 @@ cudaError_t launch_tc_cross(const void *A, int64_t M, int64_t K, int64_t lda, in
     if (mode == TC_TF32X3)
         return launch_npad<TC_TF32X3>(npad, ma, mb, p, s);
     return launch_npad<TC_TF32>(npad, ma, mb, p, s);
+}
+
+// dense BF16 tensor throughput of the MMA path above (TFLOP/s), timed with
+// CUDA events over a few launches after a warm-up; TFLOP counted as 2 M N K of
+// the MMAs issued
+cudaError_t measure_tc_peak(double *tflops, unsigned *status)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_peak, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kPeakSmem);
+        if (e != cudaSuccess)
+            return e;
+        attr = true;
+    }
+    const int sms = sm_count();
+    const int iters = 2048;   // ~1.5 ms a launch at the nominal rate
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess)
+        return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    k_tc_peak<<<sms, 128, kPeakSmem>>>(iters, status);   // warm-up
+    count_launch();
+    const int reps = 5;
+    cudaEventRecord(e0);
+    for (int i = 0; i < reps; ++i) {
+        k_tc_peak<<<sms, 128, kPeakSmem>>>(iters, status);
+        count_launch();
+    }
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess)
+        e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess)
+        return e;
+    const double flop = 2.0 * 128.0 * (2.0 * kPeakN) * 16.0 * 4.0 * iters * sms * reps;
+    *tflops = ms > 0.f ? flop / (ms * 1e-3) / 1e12 : 0.0;
+    return cudaSuccess;
 }
 
 }  // namespace nmfi

@@ -118,6 +118,7 @@ bool nnls_layout(int r, int lanes, int *G, int *J);
 cudaError_t measure_fp32_peak(double *tflops);
 // L2-resident row-gather bandwidth for rows of r floats (GB/s of gathered data)
 cudaError_t measure_l2_gather(int r, double *gbs);
+cudaError_t measure_tc_peak(double *tflops, unsigned *status);
 
 // ---- factor preparation (Gram + rescale + tensor-core packing, one launch) --
 struct PrepArgs {

@@ -749,11 +749,17 @@ def test_penalty_grid_one_iteration(h, aw, ah, bw, bh):
 
 
 def test_peak_probes(h):
-    """The two measured roofs the benchmark divides by: FP32 FFMA throughput
-    and the L2-resident row-gather bandwidth of the sparse cross term."""
+    """The measured roofs the benchmark divides by: FP32 FFMA throughput, the
+    L2-resident row-gather bandwidth of the sparse cross term, and the dense
+    BF16 rate of the library's tcgen05.mma path on an r = 512 contraction
+    (152 SMs at their 2.07 GHz maximum clock bound it near 2.6 PFLOP/s: a
+    rate above that means MMAs were not issued)."""
     tf = P.nmf_peak_fp32()
     assert 10.0 < tf < 200.0
     gbs = P.nmf_peak_l2_gather(100)
     assert 500.0 < gbs < 100000.0
     with pytest.raises(P.NmfError):
         P.nmf_peak_l2_gather(129)
+    tc = P.nmf_peak_tc_bf16(h)
+    print(f"tcgen05 bf16 r = 512 probe: {tc:.0f} TFLOP/s")
+    assert 100.0 < tc < 2600.0
