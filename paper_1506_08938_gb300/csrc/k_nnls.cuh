@@ -715,6 +715,12 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<J>()) k_nnls(const NnlsA
     extern __shared__ __align__(16) float smem[];
     float *Qs = smem;                     // RP x RP
     float *sd = Qs + RP * RP;             // scale d
+    // a dependent launch (the next half-step's cross term) may start on SMs
+    // this grid leaves and stream the data matrix, which no NQP writes; it
+    // waits for this grid to finish before it reads the packed factor.  The
+    // grid is resident at once (at most the CTAs per SM that fit), so its
+    // CTAs never wait for SMs the dependent holds.
+    pdl_trigger();
     if (!stage_qt<G, J>(a.Qt, a.d, a.r, Qs, sd, a.status))
         return;
     // this CTA's rows: a balanced contiguous range; warp w takes runs of
