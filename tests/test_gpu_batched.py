@@ -81,6 +81,20 @@ def test_launch_shapes_are_bitwise_equal(h):
         assert all(rp.iters_done == T for rp in reps)
 
 
+def test_results_do_not_depend_on_instance_order(h):
+    """The library orders its device list by cost and CTAs take work items
+    in whatever order they finish: an instance's factors and report must be
+    bitwise the same wherever it sits in the caller's list."""
+    insts = make_instances(SHAPES, seed=13)
+    T, K = 6, 3
+    ref, rref = run_batched(h, insts, T, K, "persistent")
+    perm = [5, 0, 7, 2, 6, 1, 4, 3]
+    got, rgot = run_batched(h, [insts[i] for i in perm], T, K, "persistent")
+    for j, i in enumerate(perm):
+        assert np.array_equal(got[j][0], ref[i][0]) and np.array_equal(got[j][1], ref[i][1]), i
+        assert rgot[j].objective == rref[i].objective, i
+
+
 def test_one_iteration_matches_oracle(h):
     insts = make_instances(SHAPES, seed=3)
     K = 3
