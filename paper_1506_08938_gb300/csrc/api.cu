@@ -1262,7 +1262,10 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
     const int check = o.check_every > 0 ? o.check_every : 1;
     // adaptive gap tests: from the last two tests estimate the iterations
     // still needed (gap falls roughly linearly over a few dozen iterations)
-    // and test again after about half of them
+    // and test again after 0.6 of them, at most 128 iterations on (on the FP64
+    // oracle's trajectory of the dense workload: 17 tests instead of 25 with
+    // half the estimate and 64 at most, both without passing the first
+    // iteration at the gap)
     int next_check = adaptive ? 4 : check;
     int prev_t = -1;
     double prev_gap = 0.0;
@@ -1336,9 +1339,9 @@ nmf_status solve_device(nmf_handle h, const nmf_matrix *V, const nmf_matrix *Vt,
                     if (prev_t >= 0 && prev_gap > gap) {
                         const double rate = (prev_gap - gap) / (double)(t - prev_t);
                         const double need = (gap - o.rel_gap_target) / rate;
-                        step = (int)(0.5 * need);
+                        step = (int)(0.6 * need);
                     }
-                    step = step < 1 ? 1 : (step > 64 ? 64 : step);
+                    step = step < 1 ? 1 : (step > 128 ? 128 : step);
                     prev_t = t;
                     prev_gap = gap;
                     next_check = t + 1 + step;
