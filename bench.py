@@ -284,6 +284,36 @@ def batched_measurement(P, torch, dev, h, seed, iters=20, warmup=3):
         res[mode] = {"ms_per_iter": reps[0].ms_total / iters, "launches": P.launch_count() - l0,
                      "kbar": reps[0].kbar,
                      "J_mean": float(np.mean([rp.objective for rp in reps]))}
+    # the same persistent run with the cross phase as FFMA on the CUDA cores
+    reset()
+    reps = P.nmf_solve_batched(h, dv, P.solve_opts(iters, nnls=nn, use_graph=True,
+                                                   prec="fp32_simt"), mode="persistent")
+    res["persistent_fp32_simt"] = {"ms_per_iter": reps[0].ms_total / iters, "kbar": reps[0].kbar,
+                                   "J_mean": float(np.mean([rp.objective for rp in reps]))}
+    # algorithmic FP32 work of one outer iteration (both half-steps); the
+    # cross phases read V and V^T once each
+    flops = 0.0
+    vbytes = 0.0
+    for (V, _, W, _) in dv:
+        m, n = V.shape
+        r = W.shape[1]
+        flops += 2.0 * 2.0 * m * n * r + 2.0 * r * r * (m + n)
+        vbytes += 8.0 * m * n
+    # phase by phase: one launch per phase over all instances (mode "phases")
+    # with events around every launch, 5 iterations from the start
+    peaks, _ = load_peaks()
+    phases = {}
+    for prec in ("fp32", "fp32_simt"):
+        reset()
+        P.nmf_profile_enable(True)
+        P.nmf_solve_batched(h, dv, P.solve_opts(5, nnls=nn, use_graph=False, prec=prec),
+                            mode="phases")
+        torch.cuda.synchronize()
+        ph = {c: P.nmf_profile_read(c)[0] / 5 for c in ("gram", "rescale", "cross", "nnls")}
+        P.nmf_profile_enable(False)
+        ph["cross_v_gbs"] = vbytes / (ph["cross"] * 1e-3) / 1e9
+        ph["cross_hbm_frac"] = ph["cross_v_gbs"] / peaks["hbm_gbs"]
+        phases[prec] = ph
     # ---- time to gap per instance: J*_i is instance i's objective after 400
     # iterations of the persistent form at the stricter inner tolerance eps 1e-6
     # (a GPU reference: an FP64 oracle run of all 256 instances would take
@@ -337,14 +367,6 @@ def batched_measurement(P, torch, dev, h, seed, iters=20, warmup=3):
     gap["note"] = ("persistent / loop: device time of max_i t_i iterations of the whole batch; "
                    "per-instance solve: wall time of 256 nmf_solve calls, each to its own gap "
                    "(gap tests every 10 iterations)")
-    # algorithmic FP32 work of one outer iteration (both half-steps)
-    flops = 0.0
-    vbytes = 0.0
-    for (V, _, W, _) in dv:
-        m, n = V.shape
-        r = W.shape[1]
-        flops += 2.0 * 2.0 * m * n * r + 2.0 * r * r * (m + n)
-        vbytes += 8.0 * m * n
     del dv, init
     torch.cuda.empty_cache()
     pm = res["persistent"]["ms_per_iter"]
@@ -353,8 +375,12 @@ def batched_measurement(P, torch, dev, h, seed, iters=20, warmup=3):
             "time_to_gap": gap,
             "gemm_tflops_persistent": flops / (pm * 1e-3) / 1e12,
             "v_read_gbs_persistent": vbytes / (pm * 1e-3) / 1e9,
-            "note": "FP32 on CUDA cores; ms_per_iter = device time / iterations (autotune "
-                    "includes its timed candidate iterations)"}
+            "phase_ms_per_iter": phases,
+            "note": "cross phase as 3xTF32 tcgen05 MMAs (prec fp32) unless marked fp32_simt "
+                    "(FFMA); ms_per_iter = device time / iterations (autotune includes its "
+                    "timed candidate iterations); phase_ms_per_iter: mode 'phases', events "
+                    "around each launch, first 5 iterations; cross_v_gbs = bytes of V and V^T "
+                    "/ cross-phase time"}
 
 
 def streamed_measurement(P, torch, dev, h, inst, V, Vt, W0, H0, iters=20, chunk=1024):

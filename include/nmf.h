@@ -297,12 +297,18 @@ typedef struct {
 } nmf_instance;
 
 /* Advance `count` independent instances by opts->outer_iters outer
- * iterations of Alg. 2 each (shared L1/L2 weights and NNLS options; FP32 on
- * CUDA cores).
+ * iterations of Alg. 2 each (shared L1/L2 weights and NNLS options).  The
+ * cross term's products follow opts->prec: NMF_PREC_FP32 runs them as 3xTF32
+ * tcgen05 MMAs (FP32-accurate, each 32-wide k block added into FP32 with
+ * round-to-nearest), NMF_PREC_FP32_SIMT as FFMA on the CUDA cores; any other
+ * precision returns NMF_E_NOTIMPL.  Gram, rescale and NNLS are FP32 on the
+ * CUDA cores.
  *  mode 0: persistent - one cooperative launch per outer iteration runs all
  *          eight phases (Gram, rescale, cross term, NNLS for W, then for H)
- *          for all instances with grid barriers between phases; captured in
- *          a CUDA graph when opts->use_graph;
+ *          for all instances with grid barriers between phases (with FP32
+ *          products the two cross phases run in tensor-core launches of
+ *          their own between three cooperative launches); captured in a
+ *          CUDA graph when opts->use_graph;
  *  mode 1: per-instance loop - the same phase code launched per instance and
  *          phase (the baseline);
  *  mode 2: as mode 0, with the first iterations spent timing candidate

@@ -1428,6 +1428,9 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
         return NMF_E_ARG;
     if (opts->outer_iters < 0)
         return NMF_E_ARG;
+    // FP32 products: 3xTF32 on the tensor cores, or FFMA on the CUDA cores
+    if (opts->prec != NMF_PREC_FP32 && opts->prec != NMF_PREC_FP32_SIMT)
+        return NMF_E_NOTIMPL;
     for (int i = 0; i < count; ++i) {
         const nmf_instance &b = inst[i];
         if (b.m < 1 || b.n < 1 || b.r < 1 || b.r > 64)
@@ -1515,6 +1518,9 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
     // the launches over all instances take items from the counters; the
     // one-instance launches of the loop mode keep the fixed stride
     ba.work = mode == 1 ? nullptr : dwork;
+    ba.tc = opts->prec == NMF_PREC_FP32 ? 1 : 0;
+    if (ba.tc && !batched_tc_fits())
+        return NMF_E_NOTIMPL;
 
     std::vector<int64_t> hoff;
     auto set_rows = [&](int rows) -> nmf_status {
@@ -1585,12 +1591,14 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
         ba.phase_end = 8;
         ba.inst_begin = -1;
         cudaGraphExec_t gexec = nullptr;
+        int graph_kernels = 0;
         if (opts->use_graph && t < opts->outer_iters) {
             if (!h->cap)
                 CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
             CK(cudaStreamSynchronize(s));
             prof_suspend(true);
             cudaGraph_t g = nullptr;
+            const long long l0 = g_launches.load();
             bool ok = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) ==
                       cudaSuccess;
             if (ok) {
@@ -1598,9 +1606,11 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
                 ok = (cudaStreamEndCapture(h->cap, &g) == cudaSuccess) && ok;
             }
             prof_suspend(false);
-            if (ok && g && cudaGraphInstantiate(&gexec, g, 0) == cudaSuccess) {
-                g_launches.fetch_sub(1);
-            } else {
+            // kernels per iteration: one cooperative launch, or three around
+            // the two tensor-core cross launches
+            graph_kernels = (int)(g_launches.load() - l0);
+            g_launches.fetch_sub(graph_kernels);
+            if (!(ok && g && cudaGraphInstantiate(&gexec, g, 0) == cudaSuccess)) {
                 gexec = nullptr;   // capture of a cooperative launch refused: launch directly
                 cudaGetLastError();
             }
@@ -1610,7 +1620,7 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
         for (; t < opts->outer_iters; ++t) {
             if (gexec) {
                 CK(cudaGraphLaunch(gexec, s));
-                count_launch();
+                count_launch(graph_kernels);
             } else if ((st = one_persistent())) {
                 return st;
             }

@@ -19,10 +19,14 @@
 // barriers in between (every CTA is resident: the grid is the occupancy
 // limit).  Loop mode: the same phase code launched once per instance and
 // phase, the baseline whose launch count the persistent form removes.
-// Arithmetic is FP32 on CUDA cores; instance ranks r <= 64.
+// The cross phases run on the tensor cores (3xTF32 tcgen05 MMAs with TMEM
+// accumulators, in launches of their own) or, for the FP32_SIMT precision,
+// as FFMA on the CUDA cores inside the phase kernel; the other phases are
+// FP32 on the CUDA cores.  Instance ranks r <= 64.
 #include <algorithm>
 
 #include "k_nnls.cuh"
+#include "tc_ptx.cuh"
 
 namespace nmfi {
 namespace {
@@ -277,6 +281,203 @@ __device__ void cross_item(const float *A, int64_t M, int64_t K, const float *B,
     }
 }
 
+// ---- cross term on the tensor cores ----------------------------------------
+// The same rows of C = A B as cross_item, as 3xTF32 tcgen05 MMAs: the tensor
+// core reads an FP32 operand as TF32 by dropping its low 13 bits, so the raw
+// A and B tiles serve as their own high parts, and the threads write the
+// TF32-rounded remainders (A_lo, B_lo) beside them; per 8-wide k step three
+// MMAs (M 128, N = NP) accumulate A B_hi into one TMEM column region and
+// A B_lo + A_lo B_hi into a second.  The tensor core's accumulation rounds
+// toward zero, so each 32-wide k block goes to a fresh TMEM buffer and is
+// then added into FP32 registers with round-to-nearest adds (two buffers:
+// block t accumulates while block t-1 is read).  Rows of A have any pitch,
+// so the tiles arrive by 4-byte cp.async (zero-filled outside A and B)
+// into a ring of three stages in the K-major 128B-swizzled layout (16-byte
+// chunk c of row i at chunk c ^ (i mod 8)); two k blocks are in flight
+// while the third is multiplied.
+constexpr int kTcStages = 3;
+constexpr uint32_t kTcA = 128 * 128;          // A tile: 128 rows x 32 FP32
+constexpr uint32_t kTcB = 64 * 128;           // B tile: up to 64 factor columns x 32 FP32
+constexpr uint32_t kTcStage = kTcA + kTcB;    // a multiple of 1024 (swizzle atoms)
+constexpr size_t kTcSmem = (size_t)kTcStages * kTcStage + kTcA + kTcB + 1024;   // + alignment
+constexpr uint32_t kTcCols = 256;             // TMEM: two buffers of 2 x 64 columns
+constexpr uint32_t kTcBufCols = 128;
+constexpr unsigned long long kTcWaitNs = 2000000000ull;   // 2 s: an item takes microseconds
+
+// per-CTA tensor-core state of a launch: TMEM base, the MMA-completion
+// barriers (one per TMEM buffer) and the parity each thread waits for next
+struct TcCtx {
+    uint32_t tmem;
+    uint64_t *bar;
+    uint32_t ph0, ph1;
+    volatile int *abort;
+};
+
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float *src, uint32_t bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// offset of element (row i, k) of a K-major 128B-swizzled tile of 32 FP32 per row
+__device__ __forceinline__ uint32_t sw128(int i, int k)
+{
+    return (uint32_t)(i * 128 + ((((k >> 2) ^ (i & 7))) << 4) + (k & 3) * 4);
+}
+
+template <int NP>
+__device__ bool cross_item_tc(const float *A, int64_t M, int64_t K, const float *B, int r,
+                              int64_t m0, float *C, uint8_t *tsm, TcCtx &tc)
+{
+    using namespace tcp;
+    constexpr int HC = NP / 2;                        // columns per thread per region
+    constexpr uint32_t ID = idesc(2u, 128, NP);       // TF32 x TF32 -> F32, M 128, N NP
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, half = warp >> 2;      // TMEM lane quadrant, column half
+    const int64_t KB = (K + 31) / 32;
+    const uint32_t ring = su32(tsm), lo_a = ring + kTcStages * kTcStage, lo_b = lo_a + kTcA;
+    const unsigned long long deadline = gtimer() + kTcWaitNs;
+    __syncthreads();   // the previous item is done with shared memory
+
+    auto fetch = [&](int64_t kb, int s) {
+        const int64_t k0 = kb * 32;
+        const uint32_t a0 = ring + s * kTcStage, b0 = a0 + kTcA;
+#pragma unroll
+        for (int q = 0; q < 128 * 32 / kT; ++q) {
+            const int idx = tid + kT * q, i = idx >> 5, k = idx & 31;
+            const int64_t gm = m0 + i, gk = k0 + k;
+            const bool in = gm < M && gk < K;
+            cp_async4(a0 + sw128(i, k), in ? A + gm * K + gk : A, in ? 4u : 0u);
+        }
+#pragma unroll
+        for (int q = 0; q < NP * 32 / kT; ++q) {
+            const int idx = tid + kT * q, k = idx / NP, n = idx - k * NP;
+            const int64_t gk = k0 + k;
+            const bool in = n < r && gk < K;
+            cp_async4(b0 + sw128(n, k), in ? B + gk * r + n : B, in ? 4u : 0u);
+        }
+    };
+    auto wait_mma = [&](int b) -> bool {
+        uint32_t &ph = b ? tc.ph1 : tc.ph0;
+        const bool ok = mbar_wait(tc.bar + b, ph, deadline, tc.abort);
+        ph ^= 1u;
+        return ok;
+    };
+    float acc[HC];
+#pragma unroll
+    for (int j = 0; j < HC; ++j)
+        acc[j] = 0.f;
+    auto ld_add = [&](uint32_t addr) {
+        if constexpr (HC == 32) {
+            uint32_t v[32];
+            tmem_ld32_nowait(addr, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                acc[j] += __uint_as_float(v[j]);
+        } else if constexpr (HC == 16) {
+            uint32_t v[16];
+            tmem_ld16(addr, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                acc[j] += __uint_as_float(v[j]);
+        } else {
+            uint32_t v[8];
+            tmem_ld8(addr, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                acc[j] += __uint_as_float(v[j]);
+        }
+    };
+    auto drain = [&](int b) {
+        tc_fence_after();
+        const uint32_t base = tc.tmem + b * kTcBufCols + ((uint32_t)(quad * 32) << 16) + half * HC;
+        ld_add(base);        // A B_hi
+        ld_add(base + NP);   // A B_lo + A_lo B_hi
+        tc_fence_before();
+    };
+
+    bool ok = true;
+    if (KB > 0)
+        fetch(0, 0);
+    cp_async_commit();
+    if (KB > 1)
+        fetch(1, 1);
+    cp_async_commit();
+    for (int64_t t = 0; t < KB; ++t) {
+        const int s = (int)(t % kTcStages);
+        cp_async_wait<1>();   // this thread's copies of block t have landed
+        // MMA t-1 has completed: the low-part buffers and the stage of block
+        // t + 2 (last read by MMA t-1) are free, and its TMEM buffer is ready
+        if (t > 0 && !__syncthreads_and(wait_mma((int)((t - 1) & 1)))) {
+            ok = false;
+            break;
+        }
+        if (t == 0)
+            __syncthreads();   // every thread's copies of block t are in place
+        {
+            const float4 *ha = reinterpret_cast<const float4 *>(tsm + s * kTcStage);
+            float4 *la = reinterpret_cast<float4 *>(tsm + kTcStages * kTcStage);
+            auto rem = [](float x) {
+                return rn_tf32_operand(x - __uint_as_float(__float_as_uint(x) & 0xffffe000u));
+            };
+#pragma unroll
+            for (int q = 0; q < (int)(kTcA / 16 / kT); ++q) {
+                const float4 v = ha[tid + kT * q];
+                la[tid + kT * q] = make_float4(rem(v.x), rem(v.y), rem(v.z), rem(v.w));
+            }
+            const float4 *hb = ha + kTcA / 16;
+            float4 *lb = la + kTcA / 16;
+            for (int e = tid; e < NP * 8; e += kT) {
+                const float4 v = hb[e];
+                lb[e] = make_float4(rem(v.x), rem(v.y), rem(v.z), rem(v.w));
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t d = tc.tmem + (uint32_t)(t & 1) * kTcBufCols;
+            const uint32_t a0 = ring + s * kTcStage, b0 = a0 + kTcA;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t acc_on = kk > 0 ? 1u : 0u;
+                mma<TC_TF32>(d, sdesc(a0 + 32 * kk), sdesc(b0 + 32 * kk), ID, acc_on);
+                mma<TC_TF32>(d + NP, sdesc(a0 + 32 * kk), sdesc(lo_b + 32 * kk), ID, acc_on);
+                mma<TC_TF32>(d + NP, sdesc(lo_a + 32 * kk), sdesc(b0 + 32 * kk), ID, 1u);
+            }
+            mma_commit(tc.bar + (t & 1));
+        }
+        if (t + 2 < KB)
+            fetch(t + 2, (int)((t + 2) % kTcStages));
+        cp_async_commit();
+        if (t > 0)
+            drain((int)((t - 1) & 1));
+    }
+    cp_async_wait<0>();
+    if (ok && KB > 0) {
+        if (!__syncthreads_and(wait_mma((int)((KB - 1) & 1))))
+            ok = false;
+        else
+            drain((int)((KB - 1) & 1));
+    }
+    if (!ok)
+        return false;
+    const int64_t gm = m0 + quad * 32 + lane;
+    if (gm < M) {
+#pragma unroll
+        for (int j = 0; j < HC; ++j) {
+            const int n = half * HC + j;
+            if (n < r)
+                C[gm * r + n] = acc[j];
+        }
+    }
+    return true;
+}
+
 // lanes per row of the grouped NQP solver for rank r <= 64 (J = 8 coordinates
 // per lane), and the rows of one NQP work item: `mult` rows per group of
 // every warp
@@ -410,6 +611,92 @@ __global__ void __launch_bounds__(kT, 2) k_batched_iter(const BatchArgs a)
     }
 }
 
+// One cross phase (2 or 6) on the tensor cores, in a launch of its own: the
+// streaming tiles want ~97 KB of shared memory a CTA, which in the
+// all-phase kernel would leave the NQP phases a small L1.  Items as in
+// run_phase: from the phase's counter, or a fixed stride without one.
+__global__ void __launch_bounds__(kT, 2) k_batched_cross(const BatchArgs a)
+{
+    extern __shared__ __align__(16) float smem[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t tc_bar[2];
+    __shared__ int tc_abort;
+    __shared__ unsigned long long taken;
+    if (*(const volatile unsigned *)a.status & kStTimeout)
+        return;
+    // 256 TMEM columns a CTA; at most two CTAs fit on an SM (shared memory),
+    // so the allocation of the SM's 512 columns never has to wait
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tcp::su32(&tmem_slot)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        tcp::mbar_init(&tc_bar[0], 1);
+        tcp::mbar_init(&tc_bar[1], 1);
+        tc_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tcp::tc_fence_before();
+    __syncthreads();
+    tcp::tc_fence_after();
+    TcCtx tc{tmem_slot, tc_bar, 0u, 0u, &tc_abort};
+    // the tiles start at a 1024-byte boundary (the swizzle atom)
+    uint8_t *tsm = reinterpret_cast<uint8_t *>(smem) + ((1024u - (tcp::su32(smem) & 1023u)) & 1023u);
+
+    const int phase = a.phase_begin;
+    const bool w_update = phase < 4;
+    const int64_t *off = a.item_off + (int64_t)phase * (a.count + 1);
+    const int64_t lo = a.inst_begin >= 0 ? off[a.inst_begin] : 0;
+    const int64_t hi = a.inst_begin >= 0 ? off[a.inst_begin + 1] : off[a.count];
+    if (a.work && blockIdx.x == 0 && threadIdx.x == 0)
+        a.work[(phase + 7) & 7] = 0ull;
+    int64_t item = lo + (a.work ? 0 : blockIdx.x);
+    for (;;) {
+        if (a.work) {
+            if (threadIdx.x == 0)
+                taken = atomicAdd(a.work + phase, 1ull);
+            __syncthreads();
+            item = lo + (int64_t)taken;
+            __syncthreads();
+        }
+        if (item >= hi)
+            break;
+        const int i = find_inst(off, a.count, item);
+        const BatchInst &b = a.inst[i];
+        const float *A = w_update ? b.V : b.Vt;
+        const int64_t M = w_update ? b.m : b.n, K = w_update ? b.n : b.m;
+        const float *Bm = w_update ? b.Ht : b.W;
+        float *C = w_update ? b.Cw : b.Ch;
+        const int64_t m0 = (item - off[i]) * kCrossRows;
+        bool ok;
+        if (b.r <= 16)
+            ok = cross_item_tc<16>(A, M, K, Bm, b.r, m0, C, tsm, tc);
+        else if (b.r <= 32)
+            ok = cross_item_tc<32>(A, M, K, Bm, b.r, m0, C, tsm, tc);
+        else
+            ok = cross_item_tc<64>(A, M, K, Bm, b.r, m0, C, tsm, tc);
+        if (!ok) {   // a bounded wait ran out
+            if (threadIdx.x == 0)
+                atomicOr(a.status, kStTimeout);
+            break;
+        }
+        if (!a.work)
+            item += gridDim.x;
+    }
+    // every MMA this CTA issued has been waited for (or its wait ran out)
+    tcp::tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tcp::tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem),
+                     "r"(kTcCols)
+                     : "memory");
+    }
+}
+
 }  // namespace
 
 size_t batched_smem_bytes()
@@ -460,25 +747,75 @@ int batched_grid(bool cooperative)
     return per_sm * sms;
 }
 
+// CTAs of the tensor-core cross kernel an SM holds (0 on error)
+static int cross_per_sm()
+{
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        cudaFuncSetAttribute(k_batched_cross, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTcSmem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_cross, kT,
+                                                          kTcSmem) != cudaSuccess)
+            per_sm = 0;
+    }
+    return per_sm;
+}
+
+bool batched_tc_fits()
+{
+    // every CTA an SM can hold gets its tensor-memory columns at once
+    const int p = cross_per_sm();
+    return p >= 1 && p * (int)kTcCols <= 512;
+}
+
 cudaError_t launch_batched(const BatchArgs &a, int grid, bool cooperative, cudaStream_t s)
 {
     // a launch of a single phase is attributed to that phase's kernel class
     static const KClass kPhaseClass[4] = {KC_GRAM, KC_RESCALE, KC_CROSS, KC_NNLS};
     ProfScope prof_(a.phase_end == a.phase_begin + 1 ? kPhaseClass[a.phase_begin & 3] : KC_OTHER, s);
-    const size_t smem = batched_smem_bytes();
     if (grid < 1)
         return cudaSuccess;
-    cudaError_t e;
-    if (cooperative) {
-        void *args[] = {const_cast<BatchArgs *>(&a)};
-        e = cudaLaunchCooperativeKernel((const void *)k_batched_iter, dim3(grid), dim3(kT), args,
-                                        smem, s);
-    } else {
-        k_batched_iter<<<grid, kT, smem, s>>>(a);
-        e = cudaGetLastError();
+    if (a.tc && !batched_tc_fits())
+        return cudaErrorInvalidConfiguration;
+    const size_t smem = batched_smem_bytes();
+    // the phase range in runs: tensor-core cross phases in launches of their
+    // own, the phases between them in one (cooperative) launch each
+    for (int p0 = a.phase_begin; p0 < a.phase_end;) {
+        BatchArgs b = a;
+        cudaError_t e;
+        if (a.tc && (p0 & 3) == 2) {
+            b.phase_begin = p0;
+            b.phase_end = p0 + 1;
+            int dev = 0, sms = 1;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            // over all instances: every CTA the SMs hold, items from the
+            // counter; one instance: one CTA per item (the given grid)
+            const int g = a.work ? cross_per_sm() * sms : grid;
+            k_batched_cross<<<g, kT, kTcSmem, s>>>(b);
+            e = cudaGetLastError();
+            ++p0;
+        } else {
+            int p1 = p0 + 1;
+            while (p1 < a.phase_end && !(a.tc && (p1 & 3) == 2))
+                ++p1;
+            b.phase_begin = p0;
+            b.phase_end = p1;
+            if (cooperative) {
+                void *args[] = {&b};
+                e = cudaLaunchCooperativeKernel((const void *)k_batched_iter, dim3(grid), dim3(kT),
+                                                args, smem, s);
+            } else {
+                k_batched_iter<<<grid, kT, smem, s>>>(b);
+                e = cudaGetLastError();
+            }
+            p0 = p1;
+        }
+        count_launch();
+        if (e != cudaSuccess)
+            return e;
     }
-    count_launch();
-    return e;
+    return cudaSuccess;
 }
 
 }  // namespace nmfi

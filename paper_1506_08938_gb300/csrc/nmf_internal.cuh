@@ -231,10 +231,15 @@ struct BatchArgs {
     // per-phase item counters (8): CTAs take items in order from them instead
     // of a fixed stride; null: the fixed stride (one-instance launches)
     unsigned long long *work;
+    // cross phases on the tensor cores (3xTF32, tcgen05) instead of FFMA
+    int tc;
 };
 size_t batched_smem_bytes();
 int64_t batched_items(int phase, int64_t m, int64_t n, int r, int nnls_mult);
 int batched_grid(bool cooperative);
+// the tensor-core cross phase's TMEM (256 columns a CTA) fits every CTA an
+// SM can hold
+bool batched_tc_fits();
 cudaError_t launch_batched(const BatchArgs &a, int grid, bool cooperative, cudaStream_t s);
 
 // ---- sparse cross term ----------------------------------------------------
