@@ -1440,6 +1440,14 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
     }
     CK(cudaSetDevice(h->device));
     const nmf_nnls_opts nn = opts_or_default(&opts->nnls);
+    const bool tc = opts->prec == NMF_PREC_FP32;
+    // the tensor-core cross phase copies its tiles 16 bytes at a time: an
+    // array whose rows do not start 16 bytes apart gets a row-padded copy
+    // (pitch rounded up to 4 floats), made once per call
+    auto padded = [](const float *p, int64_t cols) {
+        return (cols & 3) != 0 || (reinterpret_cast<uintptr_t>(p) & 15) != 0;
+    };
+    auto pad4 = [](int64_t c) { return (c + 3) & ~int64_t(3); };
     // ---- workspace: per-instance buffers, then the device tables
     Sizer z;
     for (int i = 0; i < count; ++i) {
@@ -1450,6 +1458,10 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
         z.add<float>(b.r);
         z.add<float>((size_t)b.m * b.r);
         z.add<float>((size_t)b.n * b.r);
+        if (tc && padded(b.V, b.n))
+            z.add<float>((size_t)b.m * pad4(b.n));
+        if (tc && padded(b.Vt, b.m))
+            z.add<float>((size_t)b.n * pad4(b.m));
     }
     z.add<BatchInst>(count);
     z.add<int64_t>((size_t)8 * (count + 1));
@@ -1491,6 +1503,24 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
         q.alpha_h = opts->alpha_h;
         q.beta_w = opts->beta_w;
         q.beta_h = opts->beta_h;
+        q.Vx = b.V;
+        q.ldvx = b.n;
+        q.Vtx = b.Vt;
+        q.ldvtx = b.m;
+        if (tc && padded(b.V, b.n)) {
+            float *c = a.take<float>((size_t)b.m * pad4(b.n));
+            CK(cudaMemcpy2DAsync(c, pad4(b.n) * sizeof(float), b.V, b.n * sizeof(float),
+                                 b.n * sizeof(float), b.m, cudaMemcpyDeviceToDevice, h->stream));
+            q.Vx = c;
+            q.ldvx = pad4(b.n);
+        }
+        if (tc && padded(b.Vt, b.m)) {
+            float *c = a.take<float>((size_t)b.n * pad4(b.m));
+            CK(cudaMemcpy2DAsync(c, pad4(b.m) * sizeof(float), b.Vt, b.m * sizeof(float),
+                                 b.m * sizeof(float), b.n, cudaMemcpyDeviceToDevice, h->stream));
+            q.Vtx = c;
+            q.ldvtx = pad4(b.m);
+        }
     }
     BatchInst *dinst = a.take<BatchInst>(count);
     int64_t *doff = a.take<int64_t>((size_t)8 * (count + 1));
@@ -1518,7 +1548,7 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
     // the launches over all instances take items from the counters; the
     // one-instance launches of the loop mode keep the fixed stride
     ba.work = mode == 1 ? nullptr : dwork;
-    ba.tc = opts->prec == NMF_PREC_FP32 ? 1 : 0;
+    ba.tc = tc ? 1 : 0;
     if (ba.tc && !batched_tc_fits())
         return NMF_E_NOTIMPL;
 

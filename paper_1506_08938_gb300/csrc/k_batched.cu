@@ -285,9 +285,10 @@ __device__ void cross_item(const float *A, int64_t M, int64_t K, const float *B,
 // The same rows of C = A B as cross_item, as 3xTF32 tcgen05 MMAs: the tensor
 // core reads an FP32 operand as TF32 by dropping its low 13 bits, so the raw
 // A and B tiles serve as their own high parts, and the threads write the
-// TF32-rounded remainders (A_lo, B_lo) beside them; per 8-wide k step three
-// MMAs (M 128, N = NP) accumulate A B_hi into one TMEM column region and
-// A B_lo + A_lo B_hi into a second.  The tensor core's accumulation rounds
+// TF32-rounded remainders (A_lo, B_lo) beside them, with a copy of B_hi
+// stacked over B_lo; per 8-wide k step one MMA (M 128, N = 2 NP) gives A B_hi
+// and A B_lo in two TMEM column regions and a second (N = NP) adds A_lo B_hi
+// to the latter.  The tensor core's accumulation rounds
 // toward zero, so each 32-wide k block goes to a fresh TMEM buffer and is
 // then added into FP32 registers with round-to-nearest adds (two buffers:
 // block t accumulates while block t-1 is read).  Rows of A have any pitch,
@@ -299,7 +300,8 @@ constexpr int kTcStages = 3;
 constexpr uint32_t kTcA = 128 * 128;          // A tile: 128 rows x 32 FP32
 constexpr uint32_t kTcB = 64 * 128;           // B tile: up to 64 factor columns x 32 FP32
 constexpr uint32_t kTcStage = kTcA + kTcB;    // a multiple of 1024 (swizzle atoms)
-constexpr size_t kTcSmem = (size_t)kTcStages * kTcStage + kTcA + kTcB + 1024;   // + alignment
+// ring, then the low parts: A_lo, B_hi stacked over B_lo; + alignment
+constexpr size_t kTcSmem = (size_t)kTcStages * kTcStage + kTcA + 2 * kTcB + 1024;
 constexpr uint32_t kTcCols = 256;             // TMEM: two buffers of 2 x 64 columns
 constexpr uint32_t kTcBufCols = 128;
 constexpr unsigned long long kTcWaitNs = 2000000000ull;   // 2 s: an item takes microseconds
@@ -318,6 +320,12 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const float *src, uint32
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes)
                  : "memory");
 }
+// 16 bytes (both addresses 16-byte aligned), zero-filled when bytes == 0
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float *src, uint32_t bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -329,35 +337,60 @@ __device__ __forceinline__ uint32_t sw128(int i, int k)
 }
 
 template <int NP>
-__device__ bool cross_item_tc(const float *A, int64_t M, int64_t K, const float *B, int r,
-                              int64_t m0, float *C, uint8_t *tsm, TcCtx &tc)
+__device__ bool cross_item_tc(const float *A, int64_t lda, int64_t M, int64_t K, const float *B,
+                              int r, int64_t m0, float *C, uint8_t *tsm, TcCtx &tc)
 {
     using namespace tcp;
     constexpr int HC = NP / 2;                        // columns per thread per region
     constexpr uint32_t ID = idesc(2u, 128, NP);       // TF32 x TF32 -> F32, M 128, N NP
+    constexpr uint32_t ID2 = idesc(2u, 128, 2 * NP);  // the same with N 2 NP
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, half = warp >> 2;      // TMEM lane quadrant, column half
     const int64_t KB = (K + 31) / 32;
     const uint32_t ring = su32(tsm), lo_a = ring + kTcStages * kTcStage, lo_b = lo_a + kTcA;
+    const uint64_t dla = sdesc(lo_a), dlb = sdesc(lo_b);   // B_hi rows, then B_lo rows
     const unsigned long long deadline = gtimer() + kTcWaitNs;
     __syncthreads();   // the previous item is done with shared memory
 
+    // Each thread's rows, columns and swizzled chunks are the same in every
+    // k block: their offsets are taken once per item.  Rows of A 16-byte
+    // aligned (pitch a multiple of 4, A aligned): lane = (row within 4,
+    // 16-byte chunk), four 16-byte copies a thread per block; else lane = k,
+    // sixteen 4-byte copies (rows warp + 8 q, whose swizzle phase is the
+    // warp's).
+    const bool vec = (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+    const int vrow = (lane >> 3) + 4 * warp, vc = lane & 7;
+    const float *pa = vec ? A + (m0 + vrow) * lda + 4 * vc : A + (m0 + warp) * lda + lane;
+    const uint32_t da = vec ? (uint32_t)(vrow * 128 + ((vc ^ (vrow & 7)) << 4))
+                            : (uint32_t)(warp * 128 + (((lane >> 2) ^ warp) << 4) + (lane & 3) * 4);
+    const int64_t left = M - m0;   // rows of this tile inside A
+    constexpr int BQ = NP * 32 / kT, BKS = kT / NP;   // B copies a thread, k rows per round
+    const int bn = tid % NP, bk = tid / NP;
+    const bool bn_in = bn < r;
+    const float *pb = B + (int64_t)bk * r + bn;
     auto fetch = [&](int64_t kb, int s) {
         const int64_t k0 = kb * 32;
         const uint32_t a0 = ring + s * kTcStage, b0 = a0 + kTcA;
+        if (vec) {
+            const bool kin = k0 + 4 * vc < K;
 #pragma unroll
-        for (int q = 0; q < 128 * 32 / kT; ++q) {
-            const int idx = tid + kT * q, i = idx >> 5, k = idx & 31;
-            const int64_t gm = m0 + i, gk = k0 + k;
-            const bool in = gm < M && gk < K;
-            cp_async4(a0 + sw128(i, k), in ? A + gm * K + gk : A, in ? 4u : 0u);
+            for (int q = 0; q < 4; ++q) {
+                const bool in = kin && vrow + 32 * q < left;
+                cp_async16(a0 + da + q * 4096, in ? pa + (32 * q) * lda + k0 : A, in ? 16u : 0u);
+            }
+        } else {
+            const bool kin = k0 + lane < K;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const bool in = kin && warp + 8 * q < left;
+                cp_async4(a0 + da + q * 1024, in ? pa + (8 * q) * lda + k0 : A, in ? 4u : 0u);
+            }
         }
 #pragma unroll
-        for (int q = 0; q < NP * 32 / kT; ++q) {
-            const int idx = tid + kT * q, k = idx / NP, n = idx - k * NP;
-            const int64_t gk = k0 + k;
-            const bool in = n < r && gk < K;
-            cp_async4(b0 + sw128(n, k), in ? B + gk * r + n : B, in ? 4u : 0u);
+        for (int q = 0; q < BQ; ++q) {
+            const int k = bk + BKS * q;
+            const bool in = bn_in && k0 + k < K;
+            cp_async4(b0 + sw128(bn, k), in ? pb + (k0 + BKS * q) * r : B, in ? 4u : 0u);
         }
     };
     auto wait_mma = [&](int b) -> bool {
@@ -430,10 +463,11 @@ __device__ bool cross_item_tc(const float *A, int64_t M, int64_t K, const float 
                 la[tid + kT * q] = make_float4(rem(v.x), rem(v.y), rem(v.z), rem(v.w));
             }
             const float4 *hb = ha + kTcA / 16;
-            float4 *lb = la + kTcA / 16;
+            float4 *lb = la + kTcA / 16;   // NP rows of B_hi, then NP rows of B_lo
             for (int e = tid; e < NP * 8; e += kT) {
                 const float4 v = hb[e];
-                lb[e] = make_float4(rem(v.x), rem(v.y), rem(v.z), rem(v.w));
+                lb[e] = v;
+                lb[NP * 8 + e] = make_float4(rem(v.x), rem(v.y), rem(v.z), rem(v.w));
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -441,13 +475,14 @@ __device__ bool cross_item_tc(const float *A, int64_t M, int64_t K, const float 
         if (tid == 0) {
             tc_fence_after();
             const uint32_t d = tc.tmem + (uint32_t)(t & 1) * kTcBufCols;
-            const uint32_t a0 = ring + s * kTcStage, b0 = a0 + kTcA;
+            // the tiles are 1024-byte aligned, so the descriptor of the k
+            // step 32 kk bytes into a row is the tile's plus 2 kk (16-byte units)
+            const uint64_t da0 = sdesc(ring + s * kTcStage), db0 = sdesc(ring + s * kTcStage + kTcA);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
                 const uint32_t acc_on = kk > 0 ? 1u : 0u;
-                mma<TC_TF32>(d, sdesc(a0 + 32 * kk), sdesc(b0 + 32 * kk), ID, acc_on);
-                mma<TC_TF32>(d + NP, sdesc(a0 + 32 * kk), sdesc(lo_b + 32 * kk), ID, acc_on);
-                mma<TC_TF32>(d + NP, sdesc(lo_a + 32 * kk), sdesc(b0 + 32 * kk), ID, 1u);
+                mma<TC_TF32>(d, da0 + 2 * kk, dlb + 2 * kk, ID2, acc_on);
+                mma<TC_TF32>(d + NP, dla + 2 * kk, db0 + 2 * kk, ID, 1u);
             }
             mma_commit(tc.bar + (t & 1));
         }
@@ -666,18 +701,19 @@ __global__ void __launch_bounds__(kT, 2) k_batched_cross(const BatchArgs a)
             break;
         const int i = find_inst(off, a.count, item);
         const BatchInst &b = a.inst[i];
-        const float *A = w_update ? b.V : b.Vt;
+        const float *A = w_update ? b.Vx : b.Vtx;
+        const int64_t lda = w_update ? b.ldvx : b.ldvtx;
         const int64_t M = w_update ? b.m : b.n, K = w_update ? b.n : b.m;
         const float *Bm = w_update ? b.Ht : b.W;
         float *C = w_update ? b.Cw : b.Ch;
         const int64_t m0 = (item - off[i]) * kCrossRows;
         bool ok;
         if (b.r <= 16)
-            ok = cross_item_tc<16>(A, M, K, Bm, b.r, m0, C, tsm, tc);
+            ok = cross_item_tc<16>(A, lda, M, K, Bm, b.r, m0, C, tsm, tc);
         else if (b.r <= 32)
-            ok = cross_item_tc<32>(A, M, K, Bm, b.r, m0, C, tsm, tc);
+            ok = cross_item_tc<32>(A, lda, M, K, Bm, b.r, m0, C, tsm, tc);
         else
-            ok = cross_item_tc<64>(A, M, K, Bm, b.r, m0, C, tsm, tc);
+            ok = cross_item_tc<64>(A, lda, M, K, Bm, b.r, m0, C, tsm, tc);
         if (!ok) {   // a bounded wait ran out
             if (threadIdx.x == 0)
                 atomicOr(a.status, kStTimeout);
@@ -754,6 +790,9 @@ static int cross_per_sm()
     if (per_sm < 0) {
         cudaFuncSetAttribute(k_batched_cross, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kTcSmem);
+        // the whole unified memory as shared memory: two CTAs per SM
+        cudaFuncSetAttribute(k_batched_cross, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_cross, kT,
                                                           kTcSmem) != cudaSuccess)
             per_sm = 0;
@@ -763,9 +802,13 @@ static int cross_per_sm()
 
 bool batched_tc_fits()
 {
-    // every CTA an SM can hold gets its tensor-memory columns at once
-    const int p = cross_per_sm();
-    return p >= 1 && p * (int)kTcCols <= 512;
+    // every CTA an SM can hold gets its tensor-memory columns at once: the
+    // shared memory of a CTA leaves room for at most two on an SM
+    int dev = 0, smem_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    return cross_per_sm() >= 1 && (size_t)smem_sm < 3 * kTcSmem &&
+           2 * (int)kTcCols <= 512;
 }
 
 cudaError_t launch_batched(const BatchArgs &a, int grid, bool cooperative, cudaStream_t s)
@@ -789,9 +832,10 @@ cudaError_t launch_batched(const BatchArgs &a, int grid, bool cooperative, cudaS
             int dev = 0, sms = 1;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            // over all instances: every CTA the SMs hold, items from the
-            // counter; one instance: one CTA per item (the given grid)
-            const int g = a.work ? cross_per_sm() * sms : grid;
+            // over all instances: two CTAs per SM (the shared memory of a CTA
+            // leaves room for no third), items from the counter; one
+            // instance: one CTA per item (the given grid)
+            const int g = a.work ? 2 * sms : grid;
             k_batched_cross<<<g, kT, kTcSmem, s>>>(b);
             e = cudaGetLastError();
             ++p0;

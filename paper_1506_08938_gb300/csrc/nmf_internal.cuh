@@ -210,6 +210,10 @@ struct BatchInst {
     float *W, *Ht;
     float *gram, *Qt, *d, *Cw, *Ch;
     float alpha_w, alpha_h, beta_w, beta_h;
+    // the tensor-core cross phase's copies of V and Vt: the caller's arrays,
+    // or row-padded copies whose rows start 16 bytes apart (pitch in floats)
+    const float *Vx, *Vtx;
+    int64_t ldvx, ldvtx;
 };
 struct BatchNnls {
     int max_inner;
