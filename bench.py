@@ -582,7 +582,7 @@ def sparse_measurement(P, torch, dev, h, seed):
             "note": "trace-identity gap tests (CSR V); BF16 values, FP32 accumulation"}
 
 
-def profile_part(part, P, WL, torch, dev, h, seed):
+def profile_part(part, P, WL, torch, dev, h, seed, batch_count=BATCH_COUNT):
     """One bounded piece of a measurement, for ncu launch lists and captures."""
     import ctypes as C
 
@@ -625,7 +625,7 @@ def profile_part(part, P, WL, torch, dev, h, seed):
         torch.cuda.nvtx.range_pop()
         srv.close()
     elif part == "batched":
-        insts = WL.batched(seed=seed, count=BATCH_COUNT, workers=max(1, os.cpu_count() or 1))
+        insts = WL.batched(seed=seed, count=batch_count, workers=max(1, os.cpu_count() or 1))
         dv = []
         for inst in insts:
             V = torch.from_numpy(inst.V).to(dev)
@@ -687,6 +687,9 @@ def main():
                          "batched iterations, 5 sparse iterations, the dense workload's "
                          "NQP launches at K = 2, or the tensor-pipe probe) inside NVTX "
                          "range 'profiled' (not nnls, tcpeak), then exit")
+    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
+                    help="instances of --profile-part batched (the first of the same seeded "
+                         "list of the many-instance workload)")
     ap.add_argument("--profile", action="store_true",
                     help="for ncu: --profile-warm warm outer iterations, then 10 inside NVTX "
                          "range 'profiled'; prints per-kernel-class times and exits")
@@ -720,7 +723,8 @@ def main():
 
     dev = torch.device("cuda", local_rank)
     if args.profile_part:
-        profile_part(args.profile_part, P, WL, torch, dev, P.Handle(local_rank), args.seed)
+        profile_part(args.profile_part, P, WL, torch, dev, P.Handle(local_rank), args.seed,
+                     args.batch_count)
         return
     inst = WL.dense(seed=args.seed)
     m, n, r = inst.m, inst.n, inst.r

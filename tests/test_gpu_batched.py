@@ -177,6 +177,14 @@ def oracle_spread(inst, T, o, kw, level=1e-7, reps=4):
     return out
 
 
+def converged_horizon(inst, T, o, kw):
+    """horizon() for the converged inner solves of `o` (stopped at its
+    absolute tolerance instead of a fixed iteration count)."""
+    Ws = [O.nmf_solve(inst.W0, inst.Ht0, t, V=inst.V, opts=o, **kw)[0] for t in (T - 2, T - 1, T)]
+    rho = np.linalg.norm(Ws[2] - Ws[1]) / max(np.linalg.norm(Ws[1] - Ws[0]), 1e-300)
+    return 1.0 / (1.0 - min(rho, 0.99))
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_converged_damped_run_stays_on_the_oracle_trajectory(h, prec):
     beta = 10.0
@@ -189,12 +197,16 @@ def test_converged_damped_run_stays_on_the_oracle_trajectory(h, prec):
         Wo, Ho, ho, _ = O.nmf_solve(inst.W0, inst.Ht0, T, V=inst.V, opts=o, **kw)
         ej = abs(rp.objective - ho[-1]) / ho[-1]
         tw, th = step_bounds(Wo, Ho, inst.r, beta, beta)
-        hz = horizon(inst, T, 20000, **kw)
+        hz = converged_horizon(inst, T, o, kw)
         print(f"{prec} {inst.name}: J {ej:.1e}, W {rel_err(W, Wo):.1e}, H {rel_err(Ht, Ho):.1e}"
               f" (bound {max(tw, th) * hz:.1e})")
         assert ej < 1e-5, inst.name
-        assert rel_err(W, Wo) < max(1e-4, max(tw, th) * hz), inst.name
-        assert rel_err(Ht, Ho) < max(1e-4, max(tw, th) * hz), inst.name
+        # the per-step FP32 bound summed over the horizon, at most 1e-3 (five
+        # times the largest error measured on either arithmetic: 1.9e-4 at
+        # r = 64, where kappa(Qt) u alone is of order 1e-4)
+        tol = max(1e-4, min(max(tw, th) * hz, 1e-3))
+        assert rel_err(W, Wo) < tol, inst.name
+        assert rel_err(Ht, Ho) < tol, inst.name
 
 
 @pytest.mark.parametrize("prec", PRECS)
