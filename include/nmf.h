@@ -305,7 +305,7 @@ typedef struct {
  * CUDA cores.  With NMF_PREC_FP32 the cross phase reads its tiles 16 bytes at
  * a time: an instance whose V rows (Vt rows) do not start 16 bytes apart -
  * n (m) not a multiple of 4, or the array not 16-byte aligned - is copied
- * once per call into a row-padded workspace array of m x round4(n)
+ * once per call into a row-padded workspace array (pad columns zeroed) of m x round4(n)
  * (n x round4(m)) floats.
  *  mode 0: persistent - one cooperative launch per outer iteration runs all
  *          eight phases (Gram, rescale, cross term, NNLS for W, then for H)

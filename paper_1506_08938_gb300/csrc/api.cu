@@ -1507,18 +1507,29 @@ NMF_API nmf_status nmf_solve_batched(nmf_handle h, int count, const nmf_instance
         q.ldvx = b.n;
         q.Vtx = b.Vt;
         q.ldvtx = b.m;
+        // the pad columns are zeroed: the cross phase copies a row's last
+        // 16-byte chunk whole, and the factor rows it meets there are zero
+        // (workspace bits left as NaN or Inf would otherwise reach the sums)
+        auto pad_copy = [&](const float *src, int64_t rows, int64_t cols) -> float * {
+            const int64_t ld = pad4(cols);
+            float *c = a.take<float>((size_t)rows * ld);
+            if (cudaMemcpy2DAsync(c, ld * sizeof(float), src, cols * sizeof(float),
+                                  cols * sizeof(float), rows, cudaMemcpyDeviceToDevice,
+                                  h->stream) != cudaSuccess ||
+                (ld > cols && cudaMemset2DAsync(c + cols, ld * sizeof(float), 0,
+                                                (ld - cols) * sizeof(float), rows,
+                                                h->stream) != cudaSuccess))
+                return nullptr;
+            return c;
+        };
         if (tc && padded(b.V, b.n)) {
-            float *c = a.take<float>((size_t)b.m * pad4(b.n));
-            CK(cudaMemcpy2DAsync(c, pad4(b.n) * sizeof(float), b.V, b.n * sizeof(float),
-                                 b.n * sizeof(float), b.m, cudaMemcpyDeviceToDevice, h->stream));
-            q.Vx = c;
+            if (!(q.Vx = pad_copy(b.V, b.m, b.n)))
+                return NMF_E_CUDA;
             q.ldvx = pad4(b.n);
         }
         if (tc && padded(b.Vt, b.m)) {
-            float *c = a.take<float>((size_t)b.n * pad4(b.m));
-            CK(cudaMemcpy2DAsync(c, pad4(b.m) * sizeof(float), b.Vt, b.m * sizeof(float),
-                                 b.m * sizeof(float), b.n, cudaMemcpyDeviceToDevice, h->stream));
-            q.Vtx = c;
+            if (!(q.Vtx = pad_copy(b.Vt, b.n, b.m)))
+                return NMF_E_CUDA;
             q.ldvtx = pad4(b.m);
         }
     }

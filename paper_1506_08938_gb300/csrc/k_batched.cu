@@ -372,14 +372,13 @@ __device__ bool cross_item_tc(const float *A, int64_t lda, int64_t M, int64_t K,
         const int64_t k0 = kb * 32;
         const uint32_t a0 = ring + s * kTcStage, b0 = a0 + kTcA;
         if (vec) {
-            // the bytes of the chunk below K: a row-padded copy's pad columns
-            // were never written, and the rest of the 16 bytes is zero-filled
-            const int64_t kl = K - (k0 + 4 * vc);
-            const uint32_t kbytes = kl >= 4 ? 16u : (kl > 0 ? (uint32_t)kl * 4u : 0u);
+            // a chunk that starts below K is copied whole: K is a multiple of
+            // 4, or the rows are a row-padded copy whose pad columns are zero
+            const bool kin = k0 + 4 * vc < K;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const bool in = kbytes != 0 && vrow + 32 * q < left;
-                cp_async16(a0 + da + q * 4096, in ? pa + (32 * q) * lda + k0 : A, in ? kbytes : 0u);
+                const bool in = kin && vrow + 32 * q < left;
+                cp_async16(a0 + da + q * 4096, in ? pa + (32 * q) * lda + k0 : A, in ? 16u : 0u);
             }
         } else {
             const bool kin = k0 + lane < K;
